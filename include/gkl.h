@@ -1,0 +1,170 @@
+/*
+ * gkl.h -- C ABI of the GB300 library for the top-k singular triplets of a
+ * centred, standardised genotype matrix held 2-bit packed in GPU memory.
+ *
+ * Method: Golub-Kahan-Lanczos (GKL) bidiagonalisation with thick restart and
+ * full (classical Gram-Schmidt applied twice) or partial reorthogonalisation,
+ * with a residual-norm convergence test (Chen, Noack, Edelman, "Fast
+ * computation of the principal components of genotype matrices in Julia",
+ * arXiv:1808.03374, section 3).
+ *
+ * Matrix.  G is n samples x m SNPs with entries 0, 1, 2 (allele counts) or
+ * missing (section 1).  Storage is SNP-major, 2 bits per entry: the codes of
+ * SNP j start at byte j*stride; sample i is in byte i>>2 at bits
+ * 2*(i&3)..2*(i&3)+1; code 3 marks a missing entry.  stride is a multiple of 16
+ * and >= ceil(n/4); entries i >= n inside a row must hold code 3.
+ * The operator is
+ *     A_ij = s_i * (g_ij - mu_j) * d_j * w_j   for observed g_ij, 0 if missing,
+ * i.e. centred by the per-SNP mean mu_j, scaled by d_j (1/SD, or 0 for a
+ * monomorphic SNP), with missing entries mean-imputed (the simplest imputation;
+ * the paper names imputation as future work, section 5).  s (per sample) and w
+ * (per SNP) are optional weights, 1 by default.
+ *
+ * Conventions for every entry point:
+ *  - Return value: GKL_OK (0) or one of the GKL_ERR_* / GKL_NOT_CONVERGED codes.
+ *    Nothing is thrown across the ABI and no call aborts the process.  After a
+ *    failure gkl_last_error() describes it.
+ *  - Pointers marked (device) must be CUDA device (or managed) memory of the
+ *    device that was current at gkl_init; pointers marked (host) are host
+ *    memory; (host or device) accepts either.
+ *  - All GPU work of a handle is ordered on the stream given to gkl_init (or
+ *    gkl_set_stream).  Calls returning results in host memory synchronise that
+ *    stream; gkl_matvec/gkl_rmatvec do not.
+ *  - A handle is not thread-safe: one host thread at a time.
+ */
+#ifndef GKL_H
+#define GKL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gkl_handle gkl_handle;
+
+/* status codes */
+#define GKL_OK 0
+#define GKL_ERR_ARG 1        /* invalid argument (sizes, alignment, null pointer) */
+#define GKL_ERR_CUDA 2       /* a CUDA runtime call or kernel launch failed */
+#define GKL_ERR_NONFINITE 3  /* a Lanczos coefficient became NaN or Inf */
+#define GKL_NOT_CONVERGED 4  /* maxit restart cycles ran out; outputs hold the best triplets so far */
+#define GKL_ERR_GAP 5        /* gradient requested for singular values closer than min_relgap */
+#define GKL_ERR_STATE 6      /* call out of order (e.g. gkl_grad before a successful gkl_svd) */
+
+/* arithmetic of the Lanczos vectors and the packed products */
+#define GKL_FP64 0
+#define GKL_FP32 1
+
+/* reorthogonalisation strategy (section 3) */
+#define GKL_REORTH_FULL 0    /* CGS2 against all previous vectors at every step */
+#define GKL_REORTH_PARTIAL 1 /* omega-recurrence estimate; CGS2 only when it exceeds omega */
+
+typedef struct gkl_opts {
+    int32_t k;          /* number of singular triplets wanted, 1 <= k < ell */
+    int32_t ell;        /* Krylov subspace size (restart length), k < ell <= min(n, m, 128) */
+    int32_t k_keep;     /* Ritz vectors kept at a thick restart; 0 = k + (ell-k)/2 */
+    int32_t reorth;     /* GKL_REORTH_FULL or GKL_REORTH_PARTIAL */
+    int32_t precision;  /* GKL_FP64 or GKL_FP32 */
+    int32_t maxit;      /* maximum restart cycles (>= 1) */
+    int32_t profile;    /* nonzero: time the packed-product kernels with CUDA events (gkl_info.ms_*) */
+    int32_t reserved;   /* must be 0 */
+    double tol;        /* converged when max_{i<k} r_i <= tol * sigma_1, r_i the Ritz residual */
+    double omega;       /* PARTIAL trigger level; 0 = 1e-8 (FP64) or sqrt(eps_fp32) (FP32) */
+    uint64_t seed;      /* counter-based generator seed for the start vector and breakdown restarts */
+    const void* v0;     /* optional start vector (device, m entries of the precision's type); NULL = random */
+} gkl_opts;
+
+typedef struct gkl_info {
+    int64_t matvec_pairs;  /* A.v and A^T.u pairs applied */
+    int32_t restarts;      /* thick restarts performed */
+    int32_t cycles;        /* Lanczos cycles run (restarts + 1) */
+    int32_t reorth_u;      /* steps whose u vector was reorthogonalised */
+    int32_t reorth_v;      /* steps whose v vector was reorthogonalised */
+    int32_t breakdowns;    /* zero Lanczos coefficients replaced by fresh vectors */
+    int32_t converged;     /* 1 if the tolerance was met */
+    double max_rel_resid;  /* max_{i<k} r_i / sigma_1 at exit */
+    double dtheta1;        /* ||Delta theta||_1 = sum_{i<k} r_i (Table 3 of the paper) */
+    double ms_total;       /* wall time of the call in milliseconds (CUDA events) */
+    int64_t launches;      /* kernels launched by the call */
+    int64_t n_mv;          /* A.v main-kernel launches timed (profile != 0) */
+    int64_t n_rmv;         /* A^T.u main-kernel launches timed (profile != 0) */
+    double ms_mv;          /* summed duration of the timed A.v main kernels */
+    double ms_rmv;         /* summed duration of the timed A^T.u main kernels */
+} gkl_info;
+
+/* Fill *o with defaults: k=10, ell=30, k_keep=0, FULL, FP64, maxit=1000,
+ * profile=0, tol=1e-10, omega=0, seed=1, v0=NULL. */
+void gkl_opts_default(gkl_opts* o);
+
+/* Per-SNP statistics of a packed matrix, computed on the GPU.
+ * packed (device): m rows of stride bytes (layout above).
+ * mu, scale (device, m doubles each, or NULL): mean of the observed codes and
+ *   1/(population SD over the observed codes), 0 when the SD is 0 or no entry
+ *   is observed (mu is then 0 too).
+ * nobs (device, m int64, or NULL): observed-entry counts.
+ * The integer sums are exact and mu = sum/nobs,
+ *   scale = 1/sqrt((nobs*sum(g^2) - sum(g)^2) / nobs^2), each op IEEE-rounded.
+ * stream: cudaStream_t or NULL for the legacy default stream.
+ * Errors: GKL_ERR_ARG for n<1, m<1, stride%16, stride*4<n, misaligned packed. */
+int gkl_colstats(const uint8_t* packed, int64_t n, int64_t m, int64_t stride,
+                 double* mu, double* scale, int64_t* nobs, void* stream);
+
+/* Create a handle on the current CUDA device.
+ * packed (device, borrowed): not copied -- the caller keeps it alive and
+ *   unchanged until gkl_destroy; must be 16-byte aligned.
+ * mu, scale (host or device, m doubles each): copied in.  If both are NULL the
+ *   handle computes them with gkl_colstats.
+ * stream: cudaStream_t (as void*) used for all later work; NULL = default.
+ * Allocates device memory for its own state (released by gkl_destroy).
+ * Errors: GKL_ERR_ARG (sizes, alignment, exactly one of mu/scale NULL),
+ *   GKL_ERR_CUDA. On error *h is NULL. */
+int gkl_init(gkl_handle** h, const uint8_t* packed, int64_t n, int64_t m, int64_t stride,
+             const double* mu, const double* scale, void* stream);
+
+/* Change the stream used by later calls on h. */
+int gkl_set_stream(gkl_handle* h, void* stream);
+
+/* Per-sample weights s (n floats) and per-SNP weights w (m floats), host or
+ * device, copied in; NULL restores weight 1 for that side. */
+int gkl_set_weights(gkl_handle* h, const float* s, const float* w);
+
+/* y = A v.  prec = GKL_FP64 (v, y double) or GKL_FP32 (float).
+ * v (device, m entries), y (device, n entries); y must not alias v.
+ * Stream-ordered; does not synchronise.  Deterministic: partial sums over SNP
+ * chunks are combined in a fixed order. */
+int gkl_matvec(gkl_handle* h, int prec, const void* v, void* y);
+
+/* x = A^T u.  prec as for gkl_matvec; u (device, n entries), x (device, m). */
+int gkl_rmatvec(gkl_handle* h, int prec, const void* u, void* x);
+
+/* Top-k singular triplets by thick-restarted GKL (section 3).
+ * sigma (host, k doubles): singular values, descending.
+ * U (device, n x k column-major, precision's type) and V (device, m x k):
+ *   left and right singular vectors; the largest-magnitude entry of each V
+ *   column is positive (first on ties) and U's column flips with it.
+ *   Either may be NULL to skip it.
+ * resid (host, k doubles, or NULL): Ritz residuals r_i = beta_ell |P_{ell,i}|,
+ *   an absolute error bound on sigma_i (section 3, convergence criteria).
+ * info (host, or NULL): counters and the final residual level.
+ * Synchronises the stream.  Returns GKL_OK, GKL_NOT_CONVERGED (outputs hold
+ * the last Ritz triplets), GKL_ERR_NONFINITE, GKL_ERR_ARG or GKL_ERR_CUDA.
+ * The triplets stay in the handle for gkl_grad. */
+int gkl_svd(gkl_handle* h, const gkl_opts* o, double* sigma, void* U, void* V,
+            double* resid, gkl_info* info);
+
+/* Release the handle and all device memory it allocated (not `packed`). */
+int gkl_destroy(gkl_handle* h);
+
+/* Message of the last failure on h (or of the last failed gkl_init when h is
+ * NULL); never NULL. */
+const char* gkl_last_error(const gkl_handle* h);
+
+/* Library version string. */
+const char* gkl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GKL_H */

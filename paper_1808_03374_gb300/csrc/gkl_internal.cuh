@@ -1,0 +1,176 @@
+// Internal declarations shared by the translation units of libgkl.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "gkl.h"
+
+#define GKL_MAX_ELL 128
+
+namespace gkl {
+
+// Scalars of one Lanczos run, resident in device memory so that the step
+// sequence needs no host round trip.  Written only by single threads of
+// "last blocks" (see epilogue.cuh) and read by later kernels in stream order.
+struct DevScal {
+    double scale_u, scale_v;  // 1/alpha_j, 1/beta_j used to normalise the new vectors
+    double anorm;             // running max of the Lanczos coefficients (lower bound on ||A||)
+    double beta_last;         // beta of the last step of a cycle (couples v_{ell})
+    double pre;               // norm before reorthogonalisation of the current vector
+    int reorth_u, reorth_v;   // reorthogonalise the current u / v vector
+    int force_u, force_v;     // force reorthogonalisation at the next step (partial mode)
+    int abort;                // 0, or ABORT_* -> remaining kernels of the cycle return at once
+    int break_side;           // 0 = u, 1 = v
+    int break_step;           // step j of the breakdown
+    int n_reorth_u, n_reorth_v;
+    unsigned counter;         // arrival counter of the last-block reductions (reset by the last block)
+};
+
+enum { ABORT_NONE = 0, ABORT_BREAKDOWN = 1, ABORT_NONFINITE = 2 };
+
+// Result block of one cycle, copied to the host once per cycle.
+struct CycleOut {
+    int conv;
+    int sweeps;
+    int pad0, pad1;
+    double maxrel;
+    double dtheta;
+    double sg[GKL_MAX_ELL];
+    double resid[GKL_MAX_ELL];
+};
+
+// Solver state passed by value to the solver kernels.
+struct Sv {
+    int64_t n, m, ldu, ldv;
+    int ell, kk, k, reorth;
+    int kk_start;             // first step of the current cycle (0, or kk after a restart)
+    int prec;                 // GKL_FP64 / GKL_FP32
+    void* U;                  // n x ell (ldu), type by prec
+    void* V;                  // m x (ell+1) (ldv)
+    double* B;                // ell x ell, column-major
+    double* muh;              // (ell+1)^2 estimates u_i^T u_k
+    double* nuh;              // (ell+1)^2 estimates v_i^T v_k
+    double* P;                // ell x ell left vectors of B (sorted)
+    double* Q;                // ell x ell right vectors of B (sorted)
+    DevScal* sc;
+    CycleOut* co;
+    double* partials;         // [max blocks][GKL_MAX_ELL + 2]
+    double* coef;             // [2][GKL_MAX_ELL + 2]
+    double eps_w;             // unit roundoff of the working precision
+    double omega;             // partial-reorthogonalisation trigger
+    double tol;
+    uint64_t seed;
+};
+
+}  // namespace gkl
+
+struct gkl_handle {
+    const uint8_t* packed;
+    int64_t n, m, stride;
+    cudaStream_t stream;
+    int device;
+    int num_sms;
+    double* mu;      // m
+    double* d;       // m
+    float* s;        // n or null
+    float* w;        // m or null
+    // scratch for the packed products (grown on demand)
+    void* scratch;
+    size_t scratch_bytes;
+    // solver workspace (grown on demand)
+    void* ws;
+    size_t ws_bytes;
+    gkl::CycleOut* host_out;  // pinned
+    char err[512];
+};
+
+namespace gkl {
+
+int set_err(gkl_handle* h, int code, const char* fmt, ...);
+int cuda_err(gkl_handle* h, cudaError_t e, const char* what);
+int ensure_scratch(gkl_handle* h, size_t bytes);
+
+// ---- packed products (packed_ops.cu)
+struct MvPlan {
+    int64_t nwords;     // ceil(n/16): 32-bit words of 16 samples
+    int tiles;          // sample tiles of the products
+    int chunks;         // SNP chunks of A.v
+    int rows_per_chunk;
+    int64_t ldp;        // leading dimension of A.v partials
+    size_t bytes_fp64;  // scratch bytes needed (FP64)
+};
+MvPlan plan_products(const gkl_handle* h);
+
+// Epilogue attached to the final reduction of a product: subtract earlier
+// basis vectors, then reduce ||y||^2 and run the solver's last-block logic.
+struct FinArgs {
+    const double* bcol;  // coefficients b_r (r < nsub) to subtract: y -= sum_r b_r W[:, r]; may be null
+    int nsub;
+    const void* W;       // basis for the subtraction
+    int64_t ldw;
+    int role;            // ROLE_* (0 = plain product, no reduction)
+    int j;
+};
+
+// ev0/ev1 (optional) are recorded around the main (partial-sum) kernel.
+// Each launcher returns the number of kernels it enqueued through *nlaunch.
+template <typename T>
+cudaError_t launch_matvec(const gkl_handle* h, const T* v, T* y, void* scratch, const Sv* sv, const FinArgs* fa,
+                          cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, int* nlaunch = nullptr);
+template <typename T>
+cudaError_t launch_rmatvec(const gkl_handle* h, const T* u, T* x, void* scratch, const Sv* sv, const FinArgs* fa,
+                           cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, int* nlaunch = nullptr);
+cudaError_t launch_colstats(const uint8_t* packed, int64_t n, int64_t m, int64_t stride, double* mu, double* scale,
+                            int64_t* nobs, cudaStream_t st);
+
+// ---- vector kernels (solver_kernels.cu)
+enum {
+    ROLE_NONE = 0,
+    ROLE_U_PRE = 1,
+    ROLE_U_POST = 2,
+    ROLE_V_PRE = 3,
+    ROLE_V_POST = 4,
+    ROLE_START = 5,
+    ROLE_REPL_U = 6,
+    ROLE_REPL_V = 7
+};
+enum { CGS_DOTS = 0, CGS_UPD_DOTS = 1, CGS_UPD_NORM = 2, CGS_FILL_DOTS = 3 };
+int cgs_grid(int64_t len, int num_sms);
+
+template <typename T>
+cudaError_t launch_cgs(const Sv& sv, cudaStream_t st, int mode, T* x, int64_t len, const T* W, int64_t ldw, int ncols,
+                       const int* cond, int role, int j, uint32_t draw, int num_sms);
+template <typename T>
+cudaError_t launch_scale(const Sv& sv, cudaStream_t st, T* x, int64_t len, const double* scale);
+template <typename T>
+cudaError_t launch_fill_random(const Sv& sv, cudaStream_t st, T* x, int64_t len, uint32_t draw, int check_abort);
+template <typename T>
+cudaError_t launch_rotate(cudaStream_t st, const T* in, int64_t ldin, int ell, const double* R, int ldr, int ncols,
+                          T* out, int64_t ldout, int64_t len);
+template <typename T>
+cudaError_t launch_sign_fix(cudaStream_t st, T* U, int64_t n, T* V, int64_t m, int k, int* signs);
+cudaError_t launch_small_svd(const Sv& sv, cudaStream_t st, int restart_ready);
+cudaError_t launch_init_state(const Sv& sv, cudaStream_t st);
+
+// ---- Philox4x32-10 (Salmon et al., SC'11) for the start vector and breakdown restarts
+__host__ __device__ inline void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * c[0], p1 = (uint64_t)0xCD9E8D57u * c[2];
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0, n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1, n3 = (uint32_t)p0;
+        c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// Uniform on (-1, 1) for index i of draw `draw`.
+__host__ __device__ inline double uniform_pm1(uint64_t seed, uint32_t draw, int64_t i) {
+    uint32_t c[4] = {(uint32_t)i, draw, 0x474B4C00u, (uint32_t)(i >> 32)};
+    philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    return ((double)c[0] + 0.5) * (2.0 / 4294967296.0) - 1.0;
+}
+
+}  // namespace gkl

@@ -1,0 +1,376 @@
+// Products with the packed, standardised genotype matrix
+//     A_ij = s_i (g_ij - mu_j) d_j w_j   (g_ij observed), 0 if missing,
+// read straight from the 2-bit SNP-major buffer (no unpacked or transposed
+// copy).  The products y = A v and x = A^T u are the per-iteration cost of
+// Golub-Kahan-Lanczos bidiagonalisation (section 3 of arXiv:1808.03374);
+// mean imputation of missing codes follows from centring (section 5 names
+// imputation as future work; this is its simplest form).
+//
+// Both products are split over (sample tile) x (SNP chunk) blocks whose
+// partial sums are combined in a fixed order by a second kernel, so results
+// are deterministic.
+#include <algorithm>
+
+#include "epilogue.cuh"
+#include "gkl_internal.cuh"
+
+namespace gkl {
+
+namespace {
+constexpr int kThreads = 256;   // threads per block of the product kernels
+constexpr int kRowBatch = 32;   // SNP rows staged per batch
+}
+
+// ------------------------------------------------------------------ stats
+
+// One warp per SNP row.  Bit planes lo = bit 0, hi = bit 1 of each code give
+// the code counts with popcounts: code 1 = lo&~hi, code 2 = hi&~lo, code 3 = lo&hi.
+__global__ void k_colstats(const uint8_t* __restrict__ packed, int64_t n, int64_t m, int64_t stride,
+                           double* __restrict__ mu, double* __restrict__ scale, int64_t* __restrict__ nobs_out) {
+    int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (row >= m) return;
+    const uint32_t* r = reinterpret_cast<const uint32_t*>(packed + row * stride);
+    const int64_t nw = stride / 4;
+    long long c1 = 0, c2 = 0, c3 = 0;
+    for (int64_t t = lane; t < nw; t += 32) {
+        uint32_t w = __ldg(r + t);
+        uint32_t lo = w & 0x55555555u, hi = (w >> 1) & 0x55555555u;
+        c1 += __popc(lo & ~hi);
+        c2 += __popc(hi & ~lo);
+        c3 += __popc(lo & hi);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+        c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+        c3 += __shfl_xor_sync(0xffffffffu, c3, o);
+    }
+    if (lane != 0) return;
+    const long long pad = stride * 4 - n;  // padding entries hold code 3
+    const long long nob = n - (c3 - pad);
+    const long long s1 = c1 + 2 * c2, s2 = c1 + 4 * c2;
+    double mj = 0.0, dj = 0.0;
+    if (nob > 0) {
+        mj = (double)s1 / (double)nob;
+        double num = (double)(nob * s2 - s1 * s1);
+        double var = num / ((double)nob * (double)nob);
+        double sd = sqrt(var);
+        dj = sd > 0.0 ? 1.0 / sd : 0.0;
+    }
+    if (mu) mu[row] = mj;
+    if (scale) scale[row] = dj;
+    if (nobs_out) nobs_out[row] = nob;
+}
+
+cudaError_t launch_colstats(const uint8_t* packed, int64_t n, int64_t m, int64_t stride, double* mu, double* scale,
+                            int64_t* nobs, cudaStream_t st) {
+    int64_t threads = m * 32;
+    unsigned blocks = (unsigned)((threads + 255) / 256);
+    k_colstats<<<blocks, 256, 0, st>>>(packed, n, m, stride, mu, scale, nobs);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ plan
+
+MvPlan plan_products(const gkl_handle* h) {
+    MvPlan p;
+    p.nwords = (h->n + 15) / 16;
+    p.tiles = (int)((p.nwords + kThreads - 1) / kThreads);
+    const int target = 4 * std::max(1, h->num_sms);
+    int chunks = std::max(1, target / p.tiles);
+    int64_t rpc = (h->m + chunks - 1) / chunks;
+    rpc = std::max<int64_t>(rpc, 64);
+    rpc = (rpc + kRowBatch - 1) / kRowBatch * kRowBatch;
+    p.rows_per_chunk = (int)rpc;
+    p.chunks = (int)((h->m + rpc - 1) / rpc);
+    p.ldp = p.nwords * 16;
+    size_t mv = (size_t)p.chunks * (size_t)p.ldp + (size_t)h->m * 4;  // partials + LUT
+    size_t rmv = 2 * (size_t)p.tiles * (size_t)h->m;
+    p.bytes_fp64 = std::max(mv, rmv) * sizeof(double) + 256;
+    return p;
+}
+
+// ------------------------------------------------------------------ A v
+
+// Per-SNP table t_j[c] = (c - mu_j) * d_j * w_j * v_j for c = 0,1,2; t_j[3] = 0
+// (missing entries contribute nothing: mean imputation).
+template <typename T>
+__global__ void k_mv_table(int64_t m, const double* __restrict__ mu, const double* __restrict__ d,
+                           const float* __restrict__ w, const T* __restrict__ v, T* __restrict__ lut) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    double cw = d[j];
+    if (w) cw *= (double)w[j];
+    double coef = cw * (double)v[j];
+    double mj = mu[j];
+    lut[4 * j + 0] = (T)((0.0 - mj) * coef);
+    lut[4 * j + 1] = (T)((1.0 - mj) * coef);
+    lut[4 * j + 2] = (T)((2.0 - mj) * coef);
+    lut[4 * j + 3] = (T)0;
+}
+
+// Partial sums over one SNP chunk: each thread owns one 32-bit word of
+// every row (16 consecutive samples) and accumulates t_j[code] over the rows
+// of its chunk.  Rows are read with coalesced 32-bit loads.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_mv_part(const uint8_t* __restrict__ packed, int64_t stride,
+                                                      int64_t nwords, int64_t m, int rpc, const T* __restrict__ lut,
+                                                      T* __restrict__ part, int64_t ldp) {
+    __shared__ T slut[kRowBatch * 4];
+    const int64_t word = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int64_t j0 = (int64_t)blockIdx.y * rpc;
+    const int64_t j1 = min(m, j0 + (int64_t)rpc);
+    const bool active = word < nwords;
+    const int64_t wstride = stride >> 2;
+    const uint32_t* base = reinterpret_cast<const uint32_t*>(packed) + (active ? word : 0);
+    T acc[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc[k] = (T)0;
+    for (int64_t jb = j0; jb < j1; jb += kRowBatch) {
+        const int nr = (int)min((int64_t)kRowBatch, j1 - jb);
+        __syncthreads();
+        for (int t = threadIdx.x; t < nr * 4; t += kThreads) slut[t] = lut[jb * 4 + t];
+        __syncthreads();
+        if (!active) continue;
+        for (int r = 0; r < nr; r += 8) {
+            uint32_t wv[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) wv[q] = (r + q < nr) ? __ldg(base + (jb + r + q) * wstride) : 0xFFFFFFFFu;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const T* L = slut + (r + q < nr ? (r + q) : 0) * 4;
+                const uint32_t wq = wv[q];
+                if (r + q < nr) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) acc[k] += L[(wq >> (2 * k)) & 3u];
+                }
+            }
+        }
+    }
+    if (!active) return;
+    T* out = part + (int64_t)blockIdx.y * ldp + word * 16;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) out[k] = acc[k];
+}
+
+__device__ inline double block_sum_to(double v, double* partials_slot) {
+    __shared__ double s_red[32];
+    v = warp_sum(v);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) s_red[w] = v;
+    __syncthreads();
+    double tot = 0.0;
+    if (threadIdx.x == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        for (int q = 0; q < nw; ++q) tot += s_red[q];
+        *partials_slot = tot;
+    }
+    return tot;
+}
+
+// Runs in the last block: combine the per-block partial norms (each thread
+// sums a fixed strided subset in order, then a fixed tree) and hand the total
+// to the solver's step logic.
+__device__ inline void finish_norm(const Sv& sv, int role, int j) {
+    __shared__ double s_w[32];
+    __shared__ double s_tot;
+    const int nb = gridDim.x * gridDim.y;
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) t += __ldcg(sv.partials + (int64_t)b * (GKL_MAX_ELL + 2));
+    t = warp_sum(t);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += s_w[q];
+        s_tot = a;
+    }
+    __syncthreads();
+    step_epilogue(sv, role, j, s_tot);
+    __syncthreads();
+    release_counter(&sv.sc->counter);
+}
+
+// Final reduction of A v over SNP chunks (fixed order), sample weights,
+// optional subtraction of earlier basis vectors, optional norm + step logic.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_mv_fin(const T* __restrict__ part, int64_t ldp, int chunks, int64_t n,
+                                                     const float* __restrict__ s, T* __restrict__ y, FinArgs fa,
+                                                     Sv sv) {
+    if (fa.role != ROLE_NONE && sv.sc->abort) return;
+    __shared__ double sb[GKL_MAX_ELL];
+    __shared__ int sidx[GKL_MAX_ELL];
+    __shared__ int snz;
+    if (threadIdx.x == 0) {
+        int c = 0;
+        for (int r = 0; r < fa.nsub; ++r) {
+            double b = fa.bcol[r];
+            if (b != 0.0) { sb[c] = b; sidx[c] = r; ++c; }
+        }
+        snz = c;
+    }
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    double sq = 0.0;
+    if (i < n) {
+        T acc = (T)0;
+        for (int c = 0; c < chunks; ++c) acc += part[(int64_t)c * ldp + i];
+        if (s) acc *= (T)s[i];
+        const T* W = static_cast<const T*>(fa.W);
+        for (int q = 0; q < snz; ++q) acc -= (T)sb[q] * W[i + (int64_t)sidx[q] * fa.ldw];
+        y[i] = acc;
+        sq = (double)acc * (double)acc;
+    }
+    if (fa.role == ROLE_NONE) return;
+    block_sum_to(sq, sv.partials + (int64_t)blockIdx.x * (GKL_MAX_ELL + 2));
+    if (arrive_last(&sv.sc->counter)) finish_norm(sv, fa.role, fa.j);
+}
+
+template <typename T>
+cudaError_t launch_matvec(const gkl_handle* h, const T* v, T* y, void* scratch, const Sv* sv, const FinArgs* fa,
+                          cudaEvent_t ev0, cudaEvent_t ev1, int* nlaunch) {
+    MvPlan p = plan_products(h);
+    T* part = static_cast<T*>(scratch);
+    T* lut = part + (size_t)p.chunks * (size_t)p.ldp;
+    cudaStream_t st = h->stream;
+    k_mv_table<T><<<(unsigned)((h->m + 255) / 256), 256, 0, st>>>(h->m, h->mu, h->d, h->w, v, lut);
+    dim3 grid((unsigned)p.tiles, (unsigned)p.chunks);
+    if (ev0) cudaEventRecord(ev0, st);
+    k_mv_part<T><<<grid, kThreads, 0, st>>>(h->packed, h->stride, p.nwords, h->m, p.rows_per_chunk, lut, part, p.ldp);
+    if (ev1) cudaEventRecord(ev1, st);
+    if (nlaunch) *nlaunch = 3;
+    FinArgs f{};
+    Sv s{};
+    if (fa) f = *fa;
+    if (sv) s = *sv;
+    k_mv_fin<T><<<(unsigned)((h->n + kThreads - 1) / kThreads), kThreads, 0, st>>>(part, p.ldp, p.chunks, h->n, h->s,
+                                                                                   y, f, s);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ A^T u
+
+// Partial sums for x_j = d_j w_j [ sum_obs g_ij u~_i - mu_j sum_obs u~_i ],
+// u~ = s o u.  Each thread holds u~ for its 16 samples in registers and
+// streams the SNP rows of its chunk; the two sums are reduced across the
+// warp by shuffles and across warps in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_rmv_part(const uint8_t* __restrict__ packed, int64_t stride, int64_t n,
+                                                       int64_t nwords, int64_t m, int rpc, const T* __restrict__ u,
+                                                       const float* __restrict__ s, T* __restrict__ p1,
+                                                       T* __restrict__ p3) {
+    __shared__ T red1[kThreads / 32][kRowBatch + 1];
+    __shared__ T red3[kThreads / 32][kRowBatch + 1];
+    const int64_t word = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const bool active = word < nwords;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T ut[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        int64_t i = word * 16 + k;
+        T val = (T)0;
+        if (active && i < n) val = s ? (T)s[i] * u[i] : u[i];
+        ut[k] = val;
+    }
+    const int64_t j0 = (int64_t)blockIdx.y * rpc;
+    const int64_t j1 = min(m, j0 + (int64_t)rpc);
+    const int64_t wstride = stride >> 2;
+    const uint32_t* base = reinterpret_cast<const uint32_t*>(packed) + (active ? word : 0);
+    for (int64_t jb = j0; jb < j1; jb += kRowBatch) {
+        const int nr = (int)min((int64_t)kRowBatch, j1 - jb);
+        for (int r = 0; r < nr; ++r) {
+            uint32_t wq = active ? __ldg(base + (jb + r) * wstride) : 0xFFFFFFFFu;
+            T a1 = (T)0, a3 = (T)0;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                uint32_t c = (wq >> (2 * k)) & 3u;
+                T hv = (c == 3u) ? (T)0 : (T)c;
+                T ov = (c == 3u) ? (T)0 : (T)1;
+                a1 += hv * ut[k];
+                a3 += ov * ut[k];
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+                a3 += __shfl_xor_sync(0xffffffffu, a3, o);
+            }
+            if (lane == 0) {
+                red1[wid][r] = a1;
+                red3[wid][r] = a3;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < nr) {
+            T t1 = (T)0, t3 = (T)0;
+#pragma unroll
+            for (int q = 0; q < kThreads / 32; ++q) {
+                t1 += red1[q][threadIdx.x];
+                t3 += red3[q][threadIdx.x];
+            }
+            p1[(int64_t)blockIdx.x * m + jb + threadIdx.x] = t1;
+            p3[(int64_t)blockIdx.x * m + jb + threadIdx.x] = t3;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_rmv_fin(const T* __restrict__ p1, const T* __restrict__ p3, int tiles,
+                                                      int64_t m, const double* __restrict__ mu,
+                                                      const double* __restrict__ d, const float* __restrict__ w,
+                                                      T* __restrict__ x, FinArgs fa, Sv sv) {
+    if (fa.role != ROLE_NONE && sv.sc->abort) return;
+    const int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    double sq = 0.0;
+    if (j < m) {
+        T s1 = (T)0, s3 = (T)0;
+        for (int t = 0; t < tiles; ++t) {
+            s1 += p1[(int64_t)t * m + j];
+            s3 += p3[(int64_t)t * m + j];
+        }
+        double dw = d[j];
+        if (w) dw *= (double)w[j];
+        T val = (T)(dw * ((double)s1 - mu[j] * (double)s3));
+        const T* W = static_cast<const T*>(fa.W);
+        for (int q = 0; q < fa.nsub; ++q) val -= (T)fa.bcol[q] * W[j + (int64_t)q * fa.ldw];
+        x[j] = val;
+        sq = (double)val * (double)val;
+    }
+    if (fa.role == ROLE_NONE) return;
+    block_sum_to(sq, sv.partials + (int64_t)blockIdx.x * (GKL_MAX_ELL + 2));
+    if (arrive_last(&sv.sc->counter)) finish_norm(sv, fa.role, fa.j);
+}
+
+template <typename T>
+cudaError_t launch_rmatvec(const gkl_handle* h, const T* u, T* x, void* scratch, const Sv* sv, const FinArgs* fa,
+                           cudaEvent_t ev0, cudaEvent_t ev1, int* nlaunch) {
+    MvPlan p = plan_products(h);
+    T* p1 = static_cast<T*>(scratch);
+    T* p3 = p1 + (size_t)p.tiles * (size_t)h->m;
+    cudaStream_t st = h->stream;
+    dim3 grid((unsigned)p.tiles, (unsigned)p.chunks);
+    if (ev0) cudaEventRecord(ev0, st);
+    k_rmv_part<T><<<grid, kThreads, 0, st>>>(h->packed, h->stride, h->n, p.nwords, h->m, p.rows_per_chunk, u, h->s, p1,
+                                             p3);
+    if (ev1) cudaEventRecord(ev1, st);
+    if (nlaunch) *nlaunch = 2;
+    FinArgs f{};
+    Sv s{};
+    if (fa) f = *fa;
+    if (sv) s = *sv;
+    k_rmv_fin<T><<<(unsigned)((h->m + kThreads - 1) / kThreads), kThreads, 0, st>>>(p1, p3, p.tiles, h->m, h->mu, h->d,
+                                                                                    h->w, x, f, s);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_matvec<float>(const gkl_handle*, const float*, float*, void*, const Sv*, const FinArgs*,
+                                          cudaEvent_t, cudaEvent_t, int*);
+template cudaError_t launch_matvec<double>(const gkl_handle*, const double*, double*, void*, const Sv*, const FinArgs*,
+                                           cudaEvent_t, cudaEvent_t, int*);
+template cudaError_t launch_rmatvec<float>(const gkl_handle*, const float*, float*, void*, const Sv*, const FinArgs*,
+                                           cudaEvent_t, cudaEvent_t, int*);
+template cudaError_t launch_rmatvec<double>(const gkl_handle*, const double*, double*, void*, const Sv*,
+                                            const FinArgs*, cudaEvent_t, cudaEvent_t, int*);
+
+}  // namespace gkl

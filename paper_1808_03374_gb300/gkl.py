@@ -1,0 +1,214 @@
+"""Thin Python binding of the C ABI in include/gkl.h (ctypes).
+
+Argument marshalling only: every step of the computation runs in libgkl's CUDA
+kernels.  PyTorch supplies device memory and the current stream.  If the
+library is missing the import of this module fails loudly; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from .build import LIB as _LIB_PATH
+
+FP64, FP32 = 0, 1
+REORTH_FULL, REORTH_PARTIAL = 0, 1
+OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, NOT_CONVERGED, ERR_GAP, ERR_STATE = range(7)
+
+_PREC = {"fp64": FP64, "fp32": FP32}
+_REORTH = {"full": REORTH_FULL, "partial": REORTH_PARTIAL}
+_DTYPE = {FP64: torch.float64, FP32: torch.float32}
+
+EXPORTS = ["gkl_version", "gkl_last_error", "gkl_opts_default", "gkl_colstats", "gkl_init", "gkl_set_stream",
+           "gkl_set_weights", "gkl_matvec", "gkl_rmatvec", "gkl_svd", "gkl_destroy"]
+
+
+class GKLError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"gkl error {code}: {msg}")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("ell", ctypes.c_int32), ("k_keep", ctypes.c_int32),
+                ("reorth", ctypes.c_int32), ("precision", ctypes.c_int32), ("maxit", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32), ("tol", ctypes.c_double), ("omega", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("v0", ctypes.c_void_p)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("matvec_pairs", ctypes.c_int64), ("restarts", ctypes.c_int32), ("cycles", ctypes.c_int32),
+                ("reorth_u", ctypes.c_int32), ("reorth_v", ctypes.c_int32), ("breakdowns", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("max_rel_resid", ctypes.c_double), ("dtheta1", ctypes.c_double),
+                ("ms_total", ctypes.c_double), ("launches", ctypes.c_int64), ("n_mv", ctypes.c_int64),
+                ("n_rmv", ctypes.c_int64), ("ms_mv", ctypes.c_double), ("ms_rmv", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    path = path or _LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgkl.so is not built ({path}); run paper_1808_03374_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    lib.gkl_version.restype = ctypes.c_char_p
+    lib.gkl_last_error.restype = ctypes.c_char_p
+    lib.gkl_last_error.argtypes = [vp]
+    lib.gkl_opts_default.argtypes = [ctypes.POINTER(Opts)]
+    lib.gkl_opts_default.restype = None
+    lib.gkl_colstats.argtypes = [vp, i64, i64, i64, vp, vp, vp, vp]
+    lib.gkl_init.argtypes = [ctypes.POINTER(vp), vp, i64, i64, i64, vp, vp, vp]
+    lib.gkl_set_stream.argtypes = [vp, vp]
+    lib.gkl_set_weights.argtypes = [vp, vp, vp]
+    lib.gkl_matvec.argtypes = [vp, i32, vp, vp]
+    lib.gkl_rmatvec.argtypes = [vp, i32, vp, vp]
+    lib.gkl_svd.argtypes = [vp, ctypes.POINTER(Opts), vp, vp, vp, vp, ctypes.POINTER(Info)]
+    lib.gkl_destroy.argtypes = [vp]
+    for f in ("gkl_colstats", "gkl_init", "gkl_set_stream", "gkl_set_weights", "gkl_matvec", "gkl_rmatvec",
+              "gkl_svd", "gkl_destroy"):
+        getattr(lib, f).restype = ctypes.c_int
+    return lib
+
+
+_LIB = None
+
+
+def lib() -> ctypes.CDLL:
+    global _LIB
+    if _LIB is None:
+        _LIB = load()
+    return _LIB
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check(code: int, h=None):
+    if code != OK:
+        raise GKLError(code, lib().gkl_last_error(h).decode())
+
+
+def colstats(packed: torch.Tensor, n: int):
+    """Per-SNP mean, 1/SD and observed count of a packed matrix (device tensors)."""
+    assert packed.is_cuda and packed.dtype == torch.uint8 and packed.dim() == 2 and packed.is_contiguous()
+    m, stride = packed.shape
+    mu = torch.empty(m, dtype=torch.float64, device=packed.device)
+    sc = torch.empty(m, dtype=torch.float64, device=packed.device)
+    nobs = torch.empty(m, dtype=torch.int64, device=packed.device)
+    _check(lib().gkl_colstats(_ptr(packed), n, m, stride, _ptr(mu), _ptr(sc), _ptr(nobs), _stream()))
+    return mu, sc, nobs
+
+
+@dataclass
+class SVDResult:
+    sigma: np.ndarray
+    U: torch.Tensor | None
+    V: torch.Tensor | None
+    resid: np.ndarray
+    info: dict
+    status: int
+
+    @property
+    def converged(self) -> bool:
+        return self.status == OK
+
+
+class GKL:
+    """Handle over a packed genotype matrix resident on the GPU (borrowed)."""
+
+    def __init__(self, packed: torch.Tensor, n: int, mu: torch.Tensor | None = None,
+                 scale: torch.Tensor | None = None):
+        assert packed.is_cuda and packed.dtype == torch.uint8 and packed.dim() == 2 and packed.is_contiguous()
+        self.packed = packed  # keeps the borrowed buffer alive
+        self.n = int(n)
+        self.m, self.stride = packed.shape
+        self.device = packed.device
+        h = ctypes.c_void_p()
+        if mu is not None:
+            mu = mu.to(self.device, torch.float64).contiguous()
+            scale = scale.to(self.device, torch.float64).contiguous()
+        with torch.cuda.device(self.device):
+            _check(lib().gkl_init(ctypes.byref(h), _ptr(packed), self.n, self.m, self.stride, _ptr(mu), _ptr(scale),
+                                  _stream()))
+        self._h = h
+        self._weights = (None, None)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gkl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _sync_stream(self):
+        lib().gkl_set_stream(self._h, _stream())
+
+    def set_weights(self, s: torch.Tensor | None = None, w: torch.Tensor | None = None):
+        self._sync_stream()
+        s = None if s is None else s.to(self.device, torch.float32).contiguous()
+        w = None if w is None else w.to(self.device, torch.float32).contiguous()
+        _check(lib().gkl_set_weights(self._h, _ptr(s), _ptr(w)), self._h)
+        self._weights = (s, w)
+
+    def matvec(self, v: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        prec = FP64 if v.dtype == torch.float64 else FP32
+        assert v.is_cuda and v.dtype in (torch.float32, torch.float64) and v.numel() == self.m and v.is_contiguous()
+        y = out if out is not None else torch.empty(self.n, dtype=v.dtype, device=self.device)
+        self._sync_stream()
+        _check(lib().gkl_matvec(self._h, prec, _ptr(v), _ptr(y)), self._h)
+        return y
+
+    def rmatvec(self, u: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        prec = FP64 if u.dtype == torch.float64 else FP32
+        assert u.is_cuda and u.dtype in (torch.float32, torch.float64) and u.numel() == self.n and u.is_contiguous()
+        x = out if out is not None else torch.empty(self.m, dtype=u.dtype, device=self.device)
+        self._sync_stream()
+        _check(lib().gkl_rmatvec(self._h, prec, _ptr(u), _ptr(x)), self._h)
+        return x
+
+    def svd(self, k: int, ell: int, reorth: str = "full", precision: str = "fp64", tol: float = 1e-10,
+            maxit: int = 1000, k_keep: int = 0, omega: float = 0.0, seed: int = 1,
+            v0: torch.Tensor | None = None, want_u: bool = True, want_v: bool = True, profile: bool = False,
+            U: torch.Tensor | None = None, V: torch.Tensor | None = None, raise_on_fail: bool = True) -> SVDResult:
+        prec = _PREC[precision]
+        dt = _DTYPE[prec]
+        o = Opts()
+        lib().gkl_opts_default(ctypes.byref(o))
+        o.k, o.ell, o.k_keep, o.reorth, o.precision, o.maxit = k, ell, k_keep, _REORTH[reorth], prec, maxit
+        o.tol, o.omega, o.seed, o.profile = tol, omega, seed, int(profile)
+        if v0 is not None:
+            v0 = v0.to(self.device, dt).contiguous()
+            o.v0 = v0.data_ptr()
+        if U is None and want_u:
+            U = torch.empty((k, self.n), dtype=dt, device=self.device)  # column-major n x k
+        if V is None and want_v:
+            V = torch.empty((k, self.m), dtype=dt, device=self.device)
+        sigma = np.zeros(k)
+        resid = np.zeros(k)
+        info = Info()
+        self._sync_stream()
+        st = lib().gkl_svd(self._h, ctypes.byref(o), sigma.ctypes.data_as(ctypes.c_void_p), _ptr(U), _ptr(V),
+                           resid.ctypes.data_as(ctypes.c_void_p), ctypes.byref(info))
+        if st not in (OK, NOT_CONVERGED) and raise_on_fail:
+            _check(st, self._h)
+        return SVDResult(sigma, None if U is None else U.T, None if V is None else V.T, resid, info.as_dict(), st)
