@@ -138,6 +138,29 @@ int gkl_matvec(gkl_handle* h, int prec, const void* v, void* y);
 /* x = A^T u.  prec as for gkl_matvec; u (device, n entries), x (device, m). */
 int gkl_rmatvec(gkl_handle* h, int prec, const void* u, void* x);
 
+/* y = A v, allocating no device memory (no handle needed).  The paper has no
+ * counterpart: this is for callers that may not call cudaMalloc -- code whose
+ * device memory is owned by a host application's own pool or arena, or loops
+ * where an allocation's possible device-wide synchronisation is not allowed.
+ * packed, mu, scale (device): as for gkl_init (mu and scale are required here;
+ *   gkl_colstats computes them).  No sample or SNP weights.
+ * prec, v (device, m entries), y (device, n entries): as for gkl_matvec.
+ * stream: cudaStream_t or NULL.
+ * Scratch: a fixed 32 MiB device array inside the library, held by every GPU
+ * that loads the library until the process exits.  A call needs
+ * (chunks * 16*ceil(n/16) + 4*m) elements of the precision's type, chunks being
+ * the SNP chunk count of the product (about 4 * SM count / ceil(n/4096));
+ * sizes beyond 32 MiB are rejected with GKL_ERR_ARG and a message that gives
+ * both numbers.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents
+ * (each call writes every element it reads, so nothing needs clearing); calls
+ * that overlap on the GPU race on it and must be serialised by the caller.
+ * Same results as gkl_matvec on the same inputs (same kernels).
+ * Errors: GKL_ERR_ARG, GKL_ERR_CUDA; message via gkl_last_error(NULL). */
+int gkl_matvec_noalloc(const uint8_t* packed, int64_t n, int64_t m, int64_t stride, const double* mu,
+                       const double* scale, int prec, const void* v, void* y, void* stream);
+
 /* Top-k singular triplets by thick-restarted GKL (section 3).
  * sigma (host, k doubles): singular values, descending.
  * U (device, n x k column-major, precision's type) and V (device, m x k):

@@ -25,7 +25,7 @@ _REORTH = {"full": REORTH_FULL, "partial": REORTH_PARTIAL}
 _DTYPE = {FP64: torch.float64, FP32: torch.float32}
 
 EXPORTS = ["gkl_version", "gkl_last_error", "gkl_opts_default", "gkl_colstats", "gkl_init", "gkl_set_stream",
-           "gkl_set_weights", "gkl_matvec", "gkl_rmatvec", "gkl_svd", "gkl_destroy"]
+           "gkl_set_weights", "gkl_matvec", "gkl_rmatvec", "gkl_svd", "gkl_destroy", "gkl_matvec_noalloc"]
 
 
 class GKLError(RuntimeError):
@@ -75,8 +75,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.gkl_rmatvec.argtypes = [vp, i32, vp, vp]
     lib.gkl_svd.argtypes = [vp, ctypes.POINTER(Opts), vp, vp, vp, vp, ctypes.POINTER(Info)]
     lib.gkl_destroy.argtypes = [vp]
+    lib.gkl_matvec_noalloc.argtypes = [vp, i64, i64, i64, vp, vp, i32, vp, vp, vp]
     for f in ("gkl_colstats", "gkl_init", "gkl_set_stream", "gkl_set_weights", "gkl_matvec", "gkl_rmatvec",
-              "gkl_svd", "gkl_destroy"):
+              "gkl_svd", "gkl_destroy", "gkl_matvec_noalloc"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
