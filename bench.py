@@ -295,6 +295,14 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "time_to_topk_ms": ms / args.steps, "pairs_per_step": pairs / args.steps,
             "max_rel_resid": infos[-1]["max_rel_resid"], "restarts": infos[-1]["restarts"],
+            "jacobi_sweeps": infos[-1]["jacobi_sweeps"], "svd_fallbacks": infos[-1]["svd_fallbacks"],
+            "svd_clusters": infos[-1]["svd_clusters"], "reorth_u": infos[-1]["reorth_u"],
+            "breakdown_ms_per_step": {
+                "A.v_main": sum(i["ms_mv"] for i in infos) / args.steps,
+                "A^T.u_main": sum(i["ms_rmv"] for i in infos) / args.steps,
+                "projected_svd": sum(i["ms_svd"] for i in infos) / args.steps,
+                "reorth": sum(i["ms_cgs"] for i in infos) / args.steps},
+            "reorth_v": infos[-1]["reorth_v"],
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": sum(i["launches"] for i in infos), "clocks": clocks}
     print(json.dumps(line), flush=True)

@@ -91,6 +91,12 @@ typedef struct gkl_info {
     int64_t n_rmv;         /* A^T.u main-kernel launches timed (profile != 0) */
     double ms_mv;          /* summed duration of the timed A.v main kernels */
     double ms_rmv;         /* summed duration of the timed A^T.u main kernels */
+    int32_t jacobi_sweeps; /* most sweeps of the projected-matrix SVD in any cycle (+1000 if the FP64 Jacobi ran) */
+    int32_t svd_fallbacks; /* cycles whose projected SVD needed the full FP64 Jacobi */
+    int32_t svd_clusters;  /* ... of which because FP32 could not separate two singular values */
+    int32_t reserved;
+    double ms_svd;         /* profile != 0: summed duration of the projected-SVD kernels */
+    double ms_cgs;         /* profile != 0: summed duration of the reorthogonalisation kernels */
 } gkl_info;
 
 /* Fill *o with defaults: k=10, ell=30, k_keep=0, FULL, FP64, maxit=1000,

@@ -90,14 +90,38 @@ struct Driver {
     int64_t launches = 0;
     // optional CUDA-event timing of the main product kernels
     bool profile = false;
-    std::vector<cudaEvent_t> ev_mv, ev_rmv;  // pairs (begin, end)
-    size_t used_mv = 0, used_rmv = 0;
-    double ms_mv = 0.0, ms_rmv = 0.0;
+    std::vector<cudaEvent_t> ev_mv, ev_rmv, ev_svd, ev_cgs;  // pairs (begin, end)
+    size_t used_mv = 0, used_rmv = 0, used_svd = 0, used_cgs = 0;
+    double ms_mv = 0.0, ms_rmv = 0.0, ms_svd = 0.0, ms_cgs = 0.0;
     int64_t n_mv = 0, n_rmv = 0;
 
     ~Driver() {
-        for (cudaEvent_t e : ev_mv) cudaEventDestroy(e);
-        for (cudaEvent_t e : ev_rmv) cudaEventDestroy(e);
+        for (auto* pool : {&ev_mv, &ev_rmv, &ev_svd, &ev_cgs})
+            for (cudaEvent_t e : *pool) cudaEventDestroy(e);
+    }
+
+    // Record the begin (end = false) or end event of a timed group.
+    void mark(std::vector<cudaEvent_t>& pool, size_t& used, bool end) {
+        if (!profile) return;
+        if (!end) {
+            cudaEvent_t b, e;
+            next_pair(pool, used, &b, &e);
+            if (b) cudaEventRecord(b, h->stream);
+        } else if (used >= 2) {
+            cudaEventRecord(pool[used - 1], h->stream);
+        }
+    }
+
+    static double sum_pairs(const std::vector<cudaEvent_t>& pool, size_t used, int64_t* count) {
+        double s = 0.0;
+        for (size_t i = 0; i + 1 < used; i += 2) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, pool[i], pool[i + 1]) == cudaSuccess) {
+                s += t;
+                if (count) ++*count;
+            }
+        }
+        return s;
     }
 
     int check(cudaError_t e, const char* what) {
@@ -123,16 +147,12 @@ struct Driver {
 
     // Add up the event pairs recorded since the last harvest (stream synchronised).
     void harvest() {
-        for (size_t i = 0; i + 1 < used_mv; i += 2) {
-            float t = 0.f;
-            if (cudaEventElapsedTime(&t, ev_mv[i], ev_mv[i + 1]) == cudaSuccess) { ms_mv += t; ++n_mv; }
-        }
-        for (size_t i = 0; i + 1 < used_rmv; i += 2) {
-            float t = 0.f;
-            if (cudaEventElapsedTime(&t, ev_rmv[i], ev_rmv[i + 1]) == cudaSuccess) { ms_rmv += t; ++n_rmv; }
-        }
+        ms_mv += sum_pairs(ev_mv, used_mv, &n_mv);
+        ms_rmv += sum_pairs(ev_rmv, used_rmv, &n_rmv);
+        ms_svd += sum_pairs(ev_svd, used_svd, nullptr);
+        ms_cgs += sum_pairs(ev_cgs, used_cgs, nullptr);
         cudaGetLastError();
-        used_mv = used_rmv = 0;
+        used_mv = used_rmv = used_svd = used_cgs = 0;
     }
 
     int cgs(int mode, T* x, int64_t len, const T* W, int64_t ldw, int ncols, const int* cond, int role, int j,
@@ -157,9 +177,11 @@ struct Driver {
         if (st) return st;
         if (j > 0) {
             const int* cond = &sv.sc->reorth_u;
+            mark(ev_cgs, used_cgs, false);
             if ((st = cgs(CGS_DOTS, y, n, U, sv.ldu, j, cond, 0, j))) return st;
             if ((st = cgs(CGS_UPD_DOTS, y, n, U, sv.ldu, j, cond, 0, j))) return st;
             if ((st = cgs(CGS_UPD_NORM, y, n, U, sv.ldu, j, cond, ROLE_U_POST, j))) return st;
+            mark(ev_cgs, used_cgs, true);
         }
         return scale(y, n, &sv.sc->scale_u);
     }
@@ -174,9 +196,11 @@ struct Driver {
         launches += nl;
         if (st) return st;
         const int* cond = &sv.sc->reorth_v;
+        mark(ev_cgs, used_cgs, false);
         if ((st = cgs(CGS_DOTS, x, m, V, sv.ldv, j + 1, cond, 0, j))) return st;
         if ((st = cgs(CGS_UPD_DOTS, x, m, V, sv.ldv, j + 1, cond, 0, j))) return st;
         if ((st = cgs(CGS_UPD_NORM, x, m, V, sv.ldv, j + 1, cond, ROLE_V_POST, j))) return st;
+        mark(ev_cgs, used_cgs, true);
         return scale(x, m, &sv.sc->scale_v);
     }
 
@@ -262,7 +286,8 @@ static int run_svd(gkl_handle* h, const gkl_opts* o, double* sigma, T* Uout, T* 
     size_t oB = take(sizeof(double) * ell * ell);
     size_t oMu = take(sizeof(double) * L * L);
     size_t oNu = take(sizeof(double) * L * L);
-    size_t oPQ = take(sizeof(double) * 4 * ell * ell);  // P, Q and the Jacobi workspace
+    size_t oPQ = take(sizeof(double) * 4 * ell * ell);  // P, Q and the FP64 Jacobi workspace
+    size_t oRw = take(sizeof(double) * 8 * ell * ell);  // refinement workspace
     size_t oSc = take(sizeof(DevScal));
     size_t oCo = take(sizeof(CycleOut));
     size_t oPart = take(sizeof(double) * maxblk * (GKL_MAX_ELL + 2));
@@ -303,6 +328,7 @@ static int run_svd(gkl_handle* h, const gkl_opts* o, double* sigma, T* Uout, T* 
     sv.nuh = reinterpret_cast<double*>(base + oNu);
     sv.P = reinterpret_cast<double*>(base + oPQ);
     sv.Q = sv.P + (size_t)ell * ell;
+    sv.rw = reinterpret_cast<double*>(base + oRw);
     sv.sc = reinterpret_cast<DevScal*>(base + oSc);
     sv.co = reinterpret_cast<CycleOut*>(base + oCo);
     sv.partials = reinterpret_cast<double*>(base + oPart);
@@ -328,7 +354,7 @@ static int run_svd(gkl_handle* h, const gkl_opts* o, double* sigma, T* Uout, T* 
 
     CycleOut* ho = h->host_out;
     DevScal hs;
-    int cycle = 0, restarts = 0;
+    int cycle = 0, restarts = 0, max_sweeps = 0;
     int pos_j = 0, pos_side = 0;
     bool converged = false;
     for (;;) {
@@ -340,12 +366,15 @@ static int run_svd(gkl_handle* h, const gkl_opts* o, double* sigma, T* Uout, T* 
             if (side == 0) side = 1;
             else { side = 0; ++j; }
         }
-        D.launches += 1;
+        D.launches += 10;  // FP32 Jacobi, 3 x 2 refinement kernels, check, final, FP64 fallback
+        D.mark(D.ev_svd, D.used_svd, false);
         if ((st = D.check(launch_small_svd(sv, h->stream, 1), "projected SVD"))) return st;
+        D.mark(D.ev_svd, D.used_svd, true);
         if ((st = D.check(cudaMemcpyAsync(ho, sv.co, sizeof(CycleOut), cudaMemcpyDeviceToHost, h->stream), "read")))
             return st;
         if ((st = D.read_state(&hs))) return st;
         D.harvest();
+        if (hs.abort == ABORT_NONE) max_sweeps = std::max(max_sweeps, ho->sweeps);
         if (hs.abort == ABORT_NONFINITE)
             return set_err(h, GKL_ERR_NONFINITE, "non-finite Lanczos coefficient at step %d (%s side)", hs.break_step,
                            hs.break_side ? "v" : "u");
@@ -413,6 +442,12 @@ static int run_svd(gkl_handle* h, const gkl_opts* o, double* sigma, T* Uout, T* 
         info->n_rmv = D.n_rmv;
         info->ms_mv = D.ms_mv;
         info->ms_rmv = D.ms_rmv;
+        info->jacobi_sweeps = max_sweeps;
+        info->svd_fallbacks = hs.n_svd_fallback;
+        info->svd_clusters = hs.n_svd_cluster;
+        info->reserved = 0;
+        info->ms_svd = D.ms_svd;
+        info->ms_cgs = D.ms_cgs;
     }
     if (!converged) {
         set_err(h, GKL_NOT_CONVERGED, "not converged after %d cycles (max rel. residual %.3e)", cycle + 1, ho->maxrel);
@@ -488,6 +523,8 @@ int gkl_init(gkl_handle** out, const uint8_t* packed, int64_t n, int64_t m, int6
     cudaError_t e = cudaMalloc(&h->mu, sizeof(double) * m);
     if (e == cudaSuccess) e = cudaMalloc(&h->d, sizeof(double) * m);
     if (e == cudaSuccess) e = cudaMallocHost(&h->host_out, sizeof(CycleOut));
+    if (e == cudaSuccess) e = cudaMalloc(&h->aux, kAuxBytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->aux, 0, kAuxBytes, h->stream);
     if (e != cudaSuccess) {
         cuda_err(nullptr, e, "gkl_init allocation");
         gkl_destroy(h);
@@ -581,6 +618,7 @@ int gkl_destroy(gkl_handle* h) {
     if (h->scratch) cudaFree(h->scratch);
     if (h->ws) cudaFree(h->ws);
     if (h->host_out) cudaFreeHost(h->host_out);
+    if (h->aux) cudaFree(h->aux);
     delete h;
     return GKL_OK;
 }

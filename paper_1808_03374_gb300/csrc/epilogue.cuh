@@ -115,22 +115,28 @@ __device__ inline void finalize_beta(const Sv& sv, int j, double b, double pre) 
 //     beta_j  nu_{j+1,k} = sum_{i<=k} B_ik mu_ji - alpha_j nu_jk          (k <= j)
 // plus a rounding term eps*(alpha_j + beta_j) of the sign of the sum
 // (Simon 1984; Larsen 1998 -- the strategy section 3 of the paper cites).
+// B has known structure: rows k < kk_start (kept Ritz vectors after a
+// restart) hold sigma_k on the diagonal and rho_k in the spike column
+// kk_start; rows k >= kk_start are bidiagonal.  The sums above therefore have
+// at most two terms each, except the column kk_start (handled by a loop).
 // Called by all threads of one block; returns max_k |estimate|.
 __device__ inline double pro_update_u(const Sv& sv, int j, double alpha) {
     const int L = sv.ell + 1;
+    const int E = sv.ell;
+    const int ks = sv.kk_start;
     const double* B = sv.B;
-    double bprev = j > 0 ? B[(j - 1) + (int64_t)j * sv.ell] : 0.0;
+    double bprev = j > ks ? B[(j - 1) + (int64_t)j * E] : 0.0;
     double mx = 0.0;
     for (int k = threadIdx.x; k < j; k += blockDim.x) {
-        double t = 0.0;
-        int lmax = min(j, sv.ell - 1);
-        for (int l = 0; l <= lmax; ++l) {
-            double b = B[k + (int64_t)l * sv.ell];
-            if (b != 0.0) t += b * sv.nuh[l + (int64_t)j * L];
-        }
-        for (int i = 0; i < j; ++i) {
-            double b = B[i + (int64_t)j * sv.ell];
-            if (b != 0.0) t -= b * sv.muh[i + (int64_t)k * L];
+        // sum_l B_kl nu_lj over row k
+        double t = B[k + (int64_t)k * E] * sv.nuh[k + (int64_t)j * L];
+        if (k < ks) t += B[k + (int64_t)ks * E] * sv.nuh[ks + (int64_t)j * L];
+        else t += B[k + (int64_t)(k + 1) * E] * sv.nuh[(k + 1) + (int64_t)j * L];
+        // sum_{i<j} B_ij mu_ik over column j
+        if (j > ks) {
+            t -= bprev * sv.muh[(j - 1) + (int64_t)k * L];
+        } else {
+            for (int i = 0; i < j; ++i) t -= B[i + (int64_t)j * E] * sv.muh[i + (int64_t)k * L];
         }
         t += copysign(sv.eps_w * (alpha + bprev), t);
         double e = t / alpha;
@@ -143,14 +149,18 @@ __device__ inline double pro_update_u(const Sv& sv, int j, double alpha) {
 
 __device__ inline double pro_update_v(const Sv& sv, int j, double beta) {
     const int L = sv.ell + 1;
+    const int E = sv.ell;
+    const int ks = sv.kk_start;
     const double* B = sv.B;
-    double alpha = B[j + (int64_t)j * sv.ell];
+    double alpha = B[j + (int64_t)j * E];
     double mx = 0.0;
     for (int k = threadIdx.x; k <= j; k += blockDim.x) {
-        double t = 0.0;
-        for (int i = 0; i <= k; ++i) {
-            double b = B[i + (int64_t)k * sv.ell];
-            if (b != 0.0) t += b * (i == j ? 1.0 : sv.muh[j + (int64_t)i * L]);
+        // sum_{i<=k} B_ik mu_ji over column k (mu_jj = 1)
+        double t = B[k + (int64_t)k * E] * (k == j ? 1.0 : sv.muh[j + (int64_t)k * L]);
+        if (k > ks) {
+            t += B[(k - 1) + (int64_t)k * E] * sv.muh[j + (int64_t)(k - 1) * L];
+        } else if (k == ks) {
+            for (int i = 0; i < k; ++i) t += B[i + (int64_t)k * E] * sv.muh[j + (int64_t)i * L];
         }
         t -= alpha * sv.nuh[j + (int64_t)k * L];
         t += copysign(sv.eps_w * (alpha + beta), t);

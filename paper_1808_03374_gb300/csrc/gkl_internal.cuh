@@ -26,6 +26,9 @@ struct DevScal {
     int break_step;           // step j of the breakdown
     int n_reorth_u, n_reorth_v;
     unsigned counter;         // arrival counter of the last-block reductions (reset by the last block)
+    int svd_fallback;         // projected SVD: 1 = FP32 + refinement does not apply, use FP64 Jacobi
+    int n_svd_fallback;       // cycles whose projected SVD used the FP64 Jacobi
+    int n_svd_cluster;        // ... of which because of clustered or tiny values
 };
 
 enum { ABORT_NONE = 0, ABORT_BREAKDOWN = 1, ABORT_NONFINITE = 2 };
@@ -54,6 +57,7 @@ struct Sv {
     double* nuh;              // (ell+1)^2 estimates v_i^T v_k
     double* P;                // ell x ell left vectors of B (sorted)
     double* Q;                // ell x ell right vectors of B (sorted)
+    double* rw;               // projected-SVD workspace: 8 ell^2 doubles (U0 V0 U1 V1 R S T sig)
     DevScal* sc;
     CycleOut* co;
     double* partials;         // [max blocks][GKL_MAX_ELL + 2]
@@ -83,6 +87,7 @@ struct gkl_handle {
     void* ws;
     size_t ws_bytes;
     gkl::CycleOut* host_out;  // pinned
+    double* aux;     // small zero-initialised device buffer: scale/sum of the tensor-core product + its counter
     char err[512];
 };
 
@@ -122,6 +127,12 @@ cudaError_t launch_matvec(const gkl_handle* h, const T* v, T* y, void* scratch, 
 template <typename T>
 cudaError_t launch_rmatvec(const gkl_handle* h, const T* u, T* x, void* scratch, const Sv* sv, const FinArgs* fa,
                            cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, int* nlaunch = nullptr);
+// Tensor-core A^T u (FP32 path, packed_mma.cu).
+size_t rmv_mma_scratch_bytes(const gkl_handle* h);
+cudaError_t launch_rmatvec_mma(const gkl_handle* h, const float* u, float* x, void* scratch, const Sv* sv,
+                               const FinArgs* fa, cudaEvent_t ev0, cudaEvent_t ev1, int* nlaunch);
+constexpr size_t kAuxBytes = 64 * 1024;
+
 cudaError_t launch_colstats(const uint8_t* packed, int64_t n, int64_t m, int64_t stride, double* mu, double* scale,
                             int64_t* nobs, cudaStream_t st);
 

@@ -87,7 +87,7 @@ MvPlan plan_products(const gkl_handle* h) {
     p.ldp = p.nwords * 16;
     size_t mv = (size_t)p.chunks * (size_t)p.ldp + (size_t)h->m * 4;  // partials + LUT
     size_t rmv = 2 * (size_t)p.tiles * (size_t)h->m;
-    p.bytes_fp64 = std::max(mv, rmv) * sizeof(double) + 256;
+    p.bytes_fp64 = std::max(std::max(mv, rmv) * sizeof(double) + 256, h->aux ? rmv_mma_scratch_bytes(h) : 0);
     return p;
 }
 
@@ -152,6 +152,81 @@ __global__ void __launch_bounds__(kThreads) k_mv_part(const uint8_t* __restrict_
     T* out = part + (int64_t)blockIdx.y * ldp + word * 16;
 #pragma unroll
     for (int k = 0; k < 16; ++k) out[k] = acc[k];
+}
+
+// FP32 A v partial sums with SNP-pair tables: for rows (a, b) the 16-entry
+// table T[c_a + 4 c_b] = t_a[c_a] + t_b[c_b] turns two codes of one sample
+// into one shared-memory lookup.  The nibble k of
+//     E = (W_a & 0x33..) | ((W_b & 0x33..) << 2)   is c_a + 4 c_b of sample 2k,
+//     O = ((W_a >> 2) & 0x33..) | (W_b & 0xCC..)    is c_a + 4 c_b of sample 2k+1.
+// All lanes of a warp read the same 16-entry table, which spans 16 banks, so
+// every lookup is a single conflict-free shared-memory wavefront.
+constexpr int kPairBatch = 64;  // row pairs staged per batch (128 rows)
+
+__global__ void __launch_bounds__(kThreads) k_mv_pair(const uint8_t* __restrict__ packed, int64_t stride,
+                                                      int64_t nwords, int64_t m, int rpc,
+                                                      const float* __restrict__ lut, float* __restrict__ part,
+                                                      int64_t ldp) {
+    __shared__ float tab[kPairBatch * 16];
+    const int64_t word = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int64_t j0 = (int64_t)blockIdx.y * rpc;
+    const int64_t j1 = min(m, j0 + (int64_t)rpc);
+    const bool active = word < nwords;
+    const int64_t wstride = stride >> 2;
+    const uint32_t* base = reinterpret_cast<const uint32_t*>(packed) + (active ? word : 0);
+    float acc[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc[k] = 0.f;
+    for (int64_t jb = j0; jb < j1; jb += 2 * kPairBatch) {
+        const int nrows = (int)min((int64_t)(2 * kPairBatch), j1 - jb);
+        const int npairs = (nrows + 1) >> 1;
+        __syncthreads();
+        for (int e = threadIdx.x; e < npairs * 16; e += kThreads) {
+            const int p = e >> 4, ca = e & 3, cb = (e >> 2) & 3;
+            const int ra = 2 * p, rb = 2 * p + 1;
+            float va = lut[(jb + ra) * 4 + ca];
+            float vb = rb < nrows ? lut[(jb + rb) * 4 + cb] : 0.f;
+            tab[e] = va + vb;
+        }
+        __syncthreads();
+        if (!active) continue;
+        // two groups of four row pairs in flight: load group p0+4 while group p0 is used
+        uint32_t wa[4], wb[4], na[4], nb[4];
+        auto load_group = [&](int p0, uint32_t (&xa)[4], uint32_t (&xb)[4]) {
+            const uint32_t* rp = base + (jb + 2 * p0) * wstride;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int ra = 2 * (p0 + q), rb = ra + 1;
+                xa[q] = (ra < nrows) ? __ldg(rp + (2 * q) * wstride) : 0xFFFFFFFFu;
+                xb[q] = (rb < nrows) ? __ldg(rp + (2 * q + 1) * wstride) : 0xFFFFFFFFu;
+            }
+        };
+        load_group(0, wa, wb);
+        for (int p0 = 0; p0 < npairs; p0 += 4) {
+            if (p0 + 4 < npairs) load_group(p0 + 4, na, nb);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (p0 + q >= npairs) break;
+                const float* T = tab + (p0 + q) * 16;
+                const uint32_t e = (wa[q] & 0x33333333u) | ((wb[q] & 0x33333333u) << 2);
+                const uint32_t o = ((wa[q] >> 2) & 0x33333333u) | (wb[q] & 0xCCCCCCCCu);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    acc[2 * k] += T[(e >> (4 * k)) & 15u];
+                    acc[2 * k + 1] += T[(o >> (4 * k)) & 15u];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                wa[q] = na[q];
+                wb[q] = nb[q];
+            }
+        }
+    }
+    if (!active) return;
+    float4* out = reinterpret_cast<float4*>(part + (int64_t)blockIdx.y * ldp + word * 16);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
 }
 
 __device__ inline double block_sum_to(double v, double* partials_slot) {
@@ -237,7 +312,13 @@ cudaError_t launch_matvec(const gkl_handle* h, const T* v, T* y, void* scratch, 
     k_mv_table<T><<<(unsigned)((h->m + 255) / 256), 256, 0, st>>>(h->m, h->mu, h->d, h->w, v, lut);
     dim3 grid((unsigned)p.tiles, (unsigned)p.chunks);
     if (ev0) cudaEventRecord(ev0, st);
-    k_mv_part<T><<<grid, kThreads, 0, st>>>(h->packed, h->stride, p.nwords, h->m, p.rows_per_chunk, lut, part, p.ldp);
+    if constexpr (sizeof(T) == sizeof(float))
+        k_mv_pair<<<grid, kThreads, 0, st>>>(h->packed, h->stride, p.nwords, h->m, p.rows_per_chunk,
+                                             reinterpret_cast<const float*>(lut), reinterpret_cast<float*>(part),
+                                             p.ldp);
+    else
+        k_mv_part<T><<<grid, kThreads, 0, st>>>(h->packed, h->stride, p.nwords, h->m, p.rows_per_chunk, lut, part,
+                                                p.ldp);
     if (ev1) cudaEventRecord(ev1, st);
     if (nlaunch) *nlaunch = 3;
     FinArgs f{};
@@ -345,6 +426,11 @@ __global__ void __launch_bounds__(kThreads) k_rmv_fin(const T* __restrict__ p1, 
 template <typename T>
 cudaError_t launch_rmatvec(const gkl_handle* h, const T* u, T* x, void* scratch, const Sv* sv, const FinArgs* fa,
                            cudaEvent_t ev0, cudaEvent_t ev1, int* nlaunch) {
+    if constexpr (sizeof(T) == sizeof(float)) {
+        if (h->aux)
+            return launch_rmatvec_mma(h, reinterpret_cast<const float*>(u), reinterpret_cast<float*>(x), scratch, sv,
+                                      fa, ev0, ev1, nlaunch);
+    }
     MvPlan p = plan_products(h);
     T* p1 = static_cast<T*>(scratch);
     T* p3 = p1 + (size_t)p.tiles * (size_t)h->m;

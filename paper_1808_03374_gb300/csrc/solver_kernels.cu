@@ -88,11 +88,16 @@ __global__ void __launch_bounds__(kCgsThreads) k_cgs(Sv sv, int mode, T* __restr
         double t = block_sum_all(sq);
         if (threadIdx.x == 0) part[0] = t;
     } else {
+        // Each lane sums its strided share in the working precision (FP32
+        // products of a vector chunk are accumulated in FP32: with two
+        // Gram-Schmidt passes the projections are removed far below FP32
+        // rounding; FP64 FMAs are scarce on this GPU), then the lane sums are
+        // combined in FP64.
         for (int k = warp; k < ncols; k += nw) {
             const T* wk = W + r0 + (int64_t)k * ldw;
-            double acc = 0.0;
-            for (int64_t t = lane; t < nr; t += 32) acc += (double)wk[t] * (double)xs[t];
-            acc = warp_sum(acc);
+            T acc_w = (T)0;
+            for (int64_t t = lane; t < nr; t += 32) acc_w += wk[t] * xs[t];
+            double acc = warp_sum((double)acc_w);
             if (lane == 0) part[k] = acc;
         }
     }
@@ -285,167 +290,14 @@ __global__ void k_init_state(Sv sv) {
         sc->break_side = sc->break_step = 0;
         sc->n_reorth_u = sc->n_reorth_v = 0;
         sc->counter = 0u;
+        sc->svd_fallback = 0;
+        sc->n_svd_fallback = 0;
+        sc->n_svd_cluster = 0;
     }
 }
 
 cudaError_t launch_init_state(const Sv& sv, cudaStream_t st) {
     k_init_state<<<1, 256, 0, st>>>(sv);
-    return cudaGetLastError();
-}
-
-// ------------------------------------------------------- projected SVD
-
-// One-sided Jacobi SVD (Hestenes) of the ell x ell projected matrix B in FP64,
-// one block.  Column pairs are rotated in round-robin order (ell/2 disjoint
-// pairs per round, one warp per pair) until a sweep applies no rotation.
-// B Q = W, sigma_c = ||W[:,c]||, P[:,c] = W[:,c]/sigma_c; columns sorted by
-// descending sigma.  Then the residual test of section 3: r_i =
-// beta_ell |P_{ell,i}|, converged when max_{i<k} r_i <= tol sigma_1; and,
-// unless converged, B is reset for a thick restart with kk Ritz vectors:
-// diag(sigma_1..sigma_kk) plus the spike column B_{i,kk} = beta_ell P_{ell,i}.
-__global__ void __launch_bounds__(512) k_small_svd(Sv sv, int restart_ready, double* __restrict__ scratch) {
-    if (sv.sc->abort) return;  // the cycle was cut short by a breakdown; the host resumes it
-    extern __shared__ double dsm[];
-    const int ell = sv.ell;
-    double* W = scratch ? scratch : dsm;
-    double* Qm = W + ell * ell;
-    __shared__ int s_rot;
-    __shared__ double s_sig[GKL_MAX_ELL];
-    __shared__ int s_rank[GKL_MAX_ELL];
-    __shared__ int s_conv;
-    for (int t = threadIdx.x; t < ell * ell; t += blockDim.x) {
-        W[t] = sv.B[t];
-        Qm[t] = (t % ell == t / ell) ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    const int N = ell + (ell & 1);
-    const int npairs = N / 2;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    int sweep = 0;
-    for (; sweep < 60; ++sweep) {
-        if (threadIdx.x == 0) s_rot = 0;
-        __syncthreads();
-        for (int rnd = 0; rnd < N - 1; ++rnd) {
-            for (int p = warp; p < npairs; p += nw) {
-                int a, b;
-                if (p == 0) {
-                    a = 0;
-                    b = 1 + rnd % (N - 1);
-                } else {
-                    a = 1 + (rnd + p) % (N - 1);
-                    b = 1 + (rnd + N - 1 - p) % (N - 1);
-                }
-                if (a >= ell || b >= ell) continue;
-                double* wa = W + a * ell;
-                double* wb = W + b * ell;
-                double al = 0.0, be = 0.0, ga = 0.0;
-                for (int r = lane; r < ell; r += 32) {
-                    double x = wa[r], y = wb[r];
-                    al += x * x;
-                    be += y * y;
-                    ga += x * y;
-                }
-                al = warp_sum(al);
-                be = warp_sum(be);
-                ga = warp_sum(ga);
-                if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
-                double zeta = (be - al) / (2.0 * ga);
-                double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-                for (int r = lane; r < ell; r += 32) {
-                    double x = wa[r], y = wb[r];
-                    wa[r] = cs * x - sn * y;
-                    wb[r] = sn * x + cs * y;
-                }
-                double* qa = Qm + a * ell;
-                double* qb = Qm + b * ell;
-                for (int r = lane; r < ell; r += 32) {
-                    double x = qa[r], y = qb[r];
-                    qa[r] = cs * x - sn * y;
-                    qb[r] = sn * x + cs * y;
-                }
-                if (lane == 0) s_rot = 1;
-            }
-            __syncthreads();
-        }
-        const int rot = s_rot;
-        __syncthreads();
-        if (!rot) break;
-    }
-    for (int c = warp; c < ell; c += nw) {
-        double s2 = 0.0;
-        for (int r = lane; r < ell; r += 32) s2 += W[r + c * ell] * W[r + c * ell];
-        s2 = warp_sum(s2);
-        if (lane == 0) s_sig[c] = sqrt(s2);
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < ell; c += blockDim.x) {
-        int rank = 0;
-        for (int e = 0; e < ell; ++e)
-            if (s_sig[e] > s_sig[c] || (s_sig[e] == s_sig[c] && e < c)) ++rank;
-        s_rank[c] = rank;
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < ell * ell; t += blockDim.x) {
-        int r = t % ell, c = t / ell;
-        int dst = s_rank[c];
-        double sg = s_sig[c];
-        sv.P[r + dst * ell] = sg > 0.0 ? W[t] / sg : 0.0;
-        sv.Q[r + dst * ell] = Qm[t];
-    }
-    for (int c = threadIdx.x; c < ell; c += blockDim.x) sv.co->sg[s_rank[c]] = s_sig[c];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const double beta = sv.sc->beta_last;
-        const double s0 = sv.co->sg[0];
-        double maxr = 0.0, sum = 0.0;
-        for (int i = 0; i < sv.k; ++i) {
-            double r = fabs(beta * sv.P[(ell - 1) + i * ell]);
-            sv.co->resid[i] = r;
-            sum += r;
-            maxr = fmax(maxr, r);
-        }
-        int conv = (maxr <= sv.tol * s0) || s0 == 0.0;
-        sv.co->conv = conv;
-        sv.co->maxrel = s0 > 0.0 ? maxr / s0 : 0.0;
-        sv.co->dtheta = sum;
-        sv.co->sweeps = sweep;
-        s_conv = conv;
-    }
-    __syncthreads();
-    if (s_conv || !restart_ready) return;
-    const int kk = sv.kk, L = ell + 1;
-    const double beta = sv.sc->beta_last;
-    for (int t = threadIdx.x; t < ell * ell; t += blockDim.x) {
-        int r = t % ell, c = t / ell;
-        double v = 0.0;
-        if (r < kk && c == r) v = sv.co->sg[r];
-        else if (r < kk && c == kk) v = beta * sv.P[(ell - 1) + r * ell];
-        sv.B[t] = v;
-    }
-    for (int t = threadIdx.x; t < L * L; t += blockDim.x) {
-        int r = t % L, c = t / L;
-        double e = (r == c) ? 1.0 : sv.eps_w;
-        sv.muh[t] = e;
-        sv.nuh[t] = e;
-    }
-    if (threadIdx.x == 0) {
-        sv.sc->force_u = 0;
-        sv.sc->force_v = 0;
-    }
-}
-
-cudaError_t launch_small_svd(const Sv& sv, cudaStream_t st, int restart_ready) {
-    size_t smem = 2 * (size_t)sv.ell * sv.ell * sizeof(double);
-    double* scratch = nullptr;
-    if (smem > 200 * 1024) {
-        scratch = sv.P + 2 * (size_t)sv.ell * sv.ell;  // workspace beyond P, Q (allocated by the driver)
-        smem = 0;
-    } else if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_small_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    k_small_svd<<<1, 512, smem, st>>>(sv, restart_ready, scratch);
     return cudaGetLastError();
 }
 

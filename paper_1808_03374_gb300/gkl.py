@@ -46,7 +46,10 @@ class Info(ctypes.Structure):
                 ("reorth_u", ctypes.c_int32), ("reorth_v", ctypes.c_int32), ("breakdowns", ctypes.c_int32),
                 ("converged", ctypes.c_int32), ("max_rel_resid", ctypes.c_double), ("dtheta1", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("launches", ctypes.c_int64), ("n_mv", ctypes.c_int64),
-                ("n_rmv", ctypes.c_int64), ("ms_mv", ctypes.c_double), ("ms_rmv", ctypes.c_double)]
+                ("n_rmv", ctypes.c_int64), ("ms_mv", ctypes.c_double), ("ms_rmv", ctypes.c_double),
+                ("jacobi_sweeps", ctypes.c_int32), ("svd_fallbacks", ctypes.c_int32),
+                ("svd_clusters", ctypes.c_int32), ("reserved", ctypes.c_int32), ("ms_svd", ctypes.c_double),
+                ("ms_cgs", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

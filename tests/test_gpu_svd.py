@@ -55,7 +55,10 @@ def run_pair(gk, g, k, ell, tol, precision, reorth, seed_v0=3, maxit=500, oracle
     return M, ref, r
 
 
-def check_against_oracle(M, ref, r, k, sig_rel, vec_eps):
+def check_against_oracle(M, ref, r, k, sig_rel, vec_eps, omega=0.0):
+    """omega: orthogonality level kept by partial reorthogonalisation; the
+    Ritz residual estimate ignores the basis's departure from orthogonality,
+    so the true residual may exceed it by up to omega * sigma_1."""
     assert r.converged, r.info
     assert np.all(np.diff(r.sigma) <= 0)
     rel = np.abs(r.sigma - ref.sigma[:k]) / ref.sigma[0]
@@ -72,7 +75,7 @@ def check_against_oracle(M, ref, r, k, sig_rel, vec_eps):
     # reported residuals bound the true ones (a-posteriori, computed by the oracle)
     for i in range(k):
         t = np.linalg.norm(M.rmatvec(U[:, i]) - r.sigma[i] * V[:, i])
-        assert t <= max(2 * r.resid[i], 0) + 50 * vec_eps * ref.sigma[0]
+        assert t <= max(2 * r.resid[i], 0) + (50 * vec_eps + omega) * ref.sigma[0]
 
 
 def test_fp64_full_two_population_workload(gk):
@@ -92,7 +95,8 @@ def test_admixture_small(gk, precision, reorth):
     M, ref, r = run_pair(gk, g, 10, 28, tol, precision, reorth)
     sig_rel = 1e-10 if precision == "fp64" else 1e-5
     vec_eps = 1e-13 if precision == "fp64" else 3e-6
-    check_against_oracle(M, ref, r, 10, sig_rel, vec_eps)
+    omega = 0.0 if reorth == "full" else (1e-8 if precision == "fp64" else 2.0 ** -12)
+    check_against_oracle(M, ref, r, 10, sig_rel, vec_eps, omega)
     if reorth == "partial":
         assert r.info["reorth_u"] < r.info["matvec_pairs"]
 
@@ -102,7 +106,7 @@ def test_tiny_ragged_and_k1(gk):
     M, ref, r = run_pair(gk, g, 1, 4, 1e-12, "fp64", "full")
     check_against_oracle(M, ref, r, 1, 1e-10, 1e-13)
     M, ref, r = run_pair(gk, g, 6, 20, 1e-12, "fp64", "partial")
-    check_against_oracle(M, ref, r, 6, 1e-10, 1e-13)
+    check_against_oracle(M, ref, r, 6, 1e-10, 1e-13, 1e-8)
 
 
 def test_breakdown_on_duplicated_samples(gk):
