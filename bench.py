@@ -48,27 +48,27 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def csrc_digest():
-    h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_1808_03374_gb300", "csrc")
-    for fn in sorted(os.listdir(d)):
-        if fn.endswith((".cu", ".cuh")):
-            with open(os.path.join(d, fn), "rb") as f:
-                h.update(fn.encode())
-                h.update(f.read())
-    return h.hexdigest()[:16]
+def source_digest(fn: str) -> str:
+    """sha256 (16 hex) of one kernel source file under csrc/."""
+    with open(os.path.join(ROOT, "paper_1808_03374_gb300", "csrc", fn), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 def ncu_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources (else None)."""
+    """DRAM bytes per launch from the committed ncu summary (profiles/traffic.json),
+    if the kernel's source file is unchanged since the capture (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
     e = d.get(workload, {}).get(kernel)
-    if not e or e.get("csrc_sha") != csrc_digest():
+    if not e:
+        return None
+    try:
+        if source_digest(e["source"]) != e.get("source_sha"):
+            return None
+    except OSError:
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -246,17 +246,20 @@ def run_ours(args):
     rmv_ms = sum(i["ms_rmv"] for i in infos) / max(1, sum(i["n_rmv"] for i in infos))
     tot_mv = sum(i["ms_mv"] for i in infos)
     tot_rmv = sum(i["ms_rmv"] for i in infos)
-    if tot_mv >= tot_rmv:
-        kname, kms, kbytes = "k_mv_part (A.v)", mv_ms, packed_bytes + 4 * m + 4 * n
-    else:
-        kname, kms, kbytes = "k_rmv_part (A^T.u)", rmv_ms, packed_bytes + 4 * n + 8 * m
+    # the FP32 path runs k_mv_pair (packed_ops.cu) and k_rmv_mma (packed_mma.cu);
+    # algorithmic bytes per launch = packed G once + the FP32 input and output vectors
+    mv = ("k_mv_pair", "packed_ops.cu", mv_ms, packed_bytes + 4 * m + 4 * n)
+    rmv = ("k_rmv_mma", "packed_mma.cu", rmv_ms, packed_bytes + 4 * n + 4 * m)
+    dom, oth = (mv, rmv) if tot_mv >= tot_rmv else (rmv, mv)
+    kname, _, kms, kbytes = dom
     achieved = kbytes / (kms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
-                "traffic": ncu_traffic(kname.split()[0], WORKLOAD),
+                "traffic": ncu_traffic(kname, WORKLOAD),
                 "algorithmic_bytes_per_launch": kbytes, "avg_launch_ms": kms,
-                "other_kernel": {"k_rmv_part (A^T.u)" if tot_mv >= tot_rmv else "k_mv_part (A.v)":
-                                 {"avg_launch_ms": rmv_ms if tot_mv >= tot_rmv else mv_ms}},
+                "other_kernel": {oth[0]: {"avg_launch_ms": oth[2],
+                                          "achieved_gbs": oth[3] / (oth[2] / 1e3) / 1e9,
+                                          "traffic": ncu_traffic(oth[0], WORKLOAD)}},
                 "share_of_step": (tot_mv + tot_rmv) / ms}
 
     # end to end through the public API with host buffers

@@ -55,6 +55,10 @@ typedef struct gkl_handle gkl_handle;
 /* arithmetic of the Lanczos vectors and the packed products */
 #define GKL_FP64 0
 #define GKL_FP32 1
+/* block form (Golub-Luk-Overton block bidiagonalisation; section 5 names block
+ * methods as future work): blocks of gkl_opts.block vectors, FP32 bases, FP64
+ * projected matrix; full block reorthogonalisation (reorth is ignored). */
+#define GKL_BLOCK 2
 
 /* reorthogonalisation strategy (section 3) */
 #define GKL_REORTH_FULL 0    /* CGS2 against all previous vectors at every step */
@@ -65,10 +69,11 @@ typedef struct gkl_opts {
     int32_t ell;        /* Krylov subspace size (restart length), k < ell <= min(n, m, 128) */
     int32_t k_keep;     /* Ritz vectors kept at a thick restart; 0 = k + (ell-k)/2 */
     int32_t reorth;     /* GKL_REORTH_FULL or GKL_REORTH_PARTIAL */
-    int32_t precision;  /* GKL_FP64 or GKL_FP32 */
+    int32_t precision;  /* GKL_FP64, GKL_FP32 or GKL_BLOCK */
     int32_t maxit;      /* maximum restart cycles (>= 1) */
     int32_t profile;    /* nonzero: time the packed-product kernels with CUDA events (gkl_info.ms_*) */
-    int32_t reserved;   /* must be 0 */
+    int32_t block;      /* GKL_BLOCK: vectors per block, 1..32 (0 = 32); ell is rounded down to a
+                           multiple of it and ell - k_keep must be one too; ignored otherwise */
     double tol;        /* converged when max_{i<k} r_i <= tol * sigma_1, r_i the Ritz residual */
     double omega;       /* PARTIAL trigger level; 0 = 1e-8 (FP64) or sqrt(eps_fp32) (FP32) */
     uint64_t seed;      /* counter-based generator seed for the start vector and breakdown restarts */
@@ -178,9 +183,30 @@ int gkl_matvec_noalloc(const uint8_t* packed, int64_t n, int64_t m, int64_t stri
  * info (host, or NULL): counters and the final residual level.
  * Synchronises the stream.  Returns GKL_OK, GKL_NOT_CONVERGED (outputs hold
  * the last Ritz triplets), GKL_ERR_NONFINITE, GKL_ERR_ARG or GKL_ERR_CUDA.
- * The triplets stay in the handle for gkl_grad. */
+ * The triplets of the FP64 / FP32 solvers stay in the handle for gkl_grad.
+ * GKL_BLOCK: U and V are float; resid holds the block residuals
+ * ||S_{s+1} P[last b rows, i]||; info->matvec_pairs counts vector pairs and
+ * info->breakdowns the directions replaced by random vectors. */
 int gkl_svd(gkl_handle* h, const gkl_opts* o, double* sigma, void* U, void* V,
             double* resid, gkl_info* info);
+
+/* Gradient of a loss L(sigma, S) on the triplets of the last converged
+ * gkl_svd of h, with respect to the per-SNP weights w and per-sample weights s
+ * of A = diag(s) A0 diag(w) (the paper has no differentiation; first-order
+ * SVD perturbation theory).  S = U diag(sigma) = A V_k are the PC scores.
+ * sigma_bar (host, k doubles, or NULL = 0): dL/dsigma_i.
+ * scores_bar (device, n x k column-major in the last solve's precision, or
+ *   NULL = 0): dL/dS.  Each nonzero column i needs sigma_i separated from the
+ *   other computed values and from the next Ritz value by min_relgap*sigma_1
+ *   (else GKL_ERR_GAP); its adjoint involves a conjugate-gradient solve on the
+ *   complement of V_k.
+ * g_w (device, m entries) and g_s (device, n entries), either may be NULL:
+ *   dL/dw and dL/ds in the last solve's precision.  Weights must be nonzero.
+ * Synchronises the stream.  Errors: GKL_ERR_STATE (no converged solve),
+ * GKL_ERR_GAP, GKL_NOT_CONVERGED (a solve did not converge), GKL_ERR_ARG,
+ * GKL_ERR_CUDA. */
+int gkl_grad(gkl_handle* h, const double* sigma_bar, const void* scores_bar, void* g_w, void* g_s,
+             double min_relgap);
 
 /* Release the handle and all device memory it allocated (not `packed`). */
 int gkl_destroy(gkl_handle* h);

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -409,17 +410,50 @@ static int run_svd(gkl_handle* h, const gkl_opts* o, double* sigma, T* Uout, T* 
         pos_j = kk;
         pos_side = 0;
     }
-    // outputs: U_ell P[:, :k], V_ell Q[:, :k], sign rule
-    T* Vo = Vout ? Vout : D.vtmp;
-    if (Uout) {
-        D.launches += 1;
-        if ((st = D.check(launch_rotate<T>(h->stream, D.U, ldu, ell, sv.P, ell, k, Uout, n, n), "U out"))) return st;
+    // outputs: U_ell P[:, :k], V_ell Q[:, :k], sign rule; the triplets stay in
+    // the handle for gkl_grad
+    h->last_valid = 0;
+    const size_t lb = sizeof(T) * (size_t)(n + m) * k;
+    if (h->last_bytes < lb) {
+        if (h->last_U) cudaFree(h->last_U);
+        h->last_U = nullptr;
+        h->last_bytes = 0;
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, lb);
+        if (e != cudaSuccess) return cuda_err(h, e, "output buffers");
+        h->last_U = p;
+        h->last_bytes = lb;
     }
-    D.launches += 3;
+    h->last_V = static_cast<char*>(h->last_U) + sizeof(T) * (size_t)n * k;
+    T* Uo = static_cast<T*>(h->last_U);
+    T* Vo = static_cast<T*>(h->last_V);
+    D.launches += 4;
+    if ((st = D.check(launch_rotate<T>(h->stream, D.U, ldu, ell, sv.P, ell, k, Uo, n, n), "U out"))) return st;
     if ((st = D.check(launch_rotate<T>(h->stream, D.V, ldv, ell, sv.Q, ell, k, Vo, m, m), "V out"))) return st;
-    if ((st = D.check(launch_sign_fix<T>(h->stream, Uout, n, Vo, m, k, D.signs), "sign"))) return st;
+    if ((st = D.check(launch_sign_fix<T>(h->stream, Uo, n, Vo, m, k, D.signs), "sign"))) return st;
+    if (Uout && (st = D.check(cudaMemcpyAsync(Uout, Uo, sizeof(T) * n * k, cudaMemcpyDeviceToDevice, h->stream),
+                              "U copy")))
+        return st;
+    if (Vout && (st = D.check(cudaMemcpyAsync(Vout, Vo, sizeof(T) * m * k, cudaMemcpyDeviceToDevice, h->stream),
+                              "V copy")))
+        return st;
     cudaEventRecord(wall.b, h->stream);
     if ((st = D.check(cudaStreamSynchronize(h->stream), "final sync"))) return st;
+    if (h->tc_state > 0 && sizeof(T) == sizeof(float)) {
+        int terr = 0;
+        int* ew = reinterpret_cast<int*>(reinterpret_cast<char*>(h->aux) + kAuxErrOffset);
+        cudaMemcpyAsync(&terr, ew, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+        if ((st = D.check(cudaStreamSynchronize(h->stream), "error word"))) return st;
+        if (terr) {
+            cudaMemsetAsync(ew, 0, sizeof(int), h->stream);
+            return set_err(h, GKL_ERR_CUDA, "tensor-core A^T u: a pipeline wait ran out (code %d)", terr);
+        }
+    }
+    h->last_valid = converged ? 1 : 0;
+    h->last_prec = sizeof(T) == 8 ? GKL_FP64 : GKL_FP32;
+    h->last_k = k;
+    for (int i = 0; i < k; ++i) h->last_sigma[i] = ho->sg[i];
+    h->last_next = k < ell ? ho->sg[k] : 0.0;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, wall.a, wall.b);
     for (int i = 0; i < k; ++i) {
@@ -475,7 +509,7 @@ void gkl_opts_default(gkl_opts* o) {
     o->precision = GKL_FP64;
     o->maxit = 1000;
     o->profile = 0;
-    o->reserved = 0;
+    o->block = 0;
     o->tol = 1e-10;
     o->omega = 0.0;
     o->seed = 1;
@@ -530,6 +564,13 @@ int gkl_init(gkl_handle** out, const uint8_t* packed, int64_t n, int64_t m, int6
         gkl_destroy(h);
         return GKL_ERR_CUDA;
     }
+    // FP32 A^T u: GKL_RMV_KERNEL=tc selects the tcgen05 kernel, otherwise the
+    // mma.sync kernel runs
+    const char* rk = std::getenv("GKL_RMV_KERNEL");
+    if (rk && std::strcmp(rk, "tc") == 0)
+        tc_prepare(h);
+    else
+        h->tc_state = -1;
     if (mu) {
         e = cudaMemcpyAsync(h->mu, mu, sizeof(double) * m, cudaMemcpyDefault, h->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->d, scale, sizeof(double) * m, cudaMemcpyDefault, h->stream);
@@ -606,6 +647,7 @@ int gkl_svd(gkl_handle* h, const gkl_opts* o, double* sigma, void* U, void* V, d
     if (o->precision == GKL_FP64)
         return run_svd<double>(h, o, sigma, (double*)U, (double*)V, resid, info);
     if (o->precision == GKL_FP32) return run_svd<float>(h, o, sigma, (float*)U, (float*)V, resid, info);
+    if (o->precision == GKL_BLOCK) return run_block(h, o, sigma, (float*)U, (float*)V, resid, info);
     return set_err(h, GKL_ERR_ARG, "unknown precision %d", o->precision);
 }
 
@@ -619,6 +661,8 @@ int gkl_destroy(gkl_handle* h) {
     if (h->ws) cudaFree(h->ws);
     if (h->host_out) cudaFreeHost(h->host_out);
     if (h->aux) cudaFree(h->aux);
+    if (h->last_U) cudaFree(h->last_U);
+    if (h->gws) cudaFree(h->gws);
     delete h;
     return GKL_OK;
 }

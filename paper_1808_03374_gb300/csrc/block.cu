@@ -1,0 +1,567 @@
+// Block form of thick-restarted GKL bidiagonalisation (Golub, Luk & Overton's
+// block Lanczos bidiagonalisation, named as future work in section 5 of
+// arXiv:1808.03374; the restart follows the paper's thick restart of section 3
+// with a spike block in place of the spike column).
+//
+// Blocks of b columns, FP32 bases, FP64 projected quantities:
+//   W = A V_j - U_{j-1} S_j^T            (after a restart: - U_kept C, C the spike block)
+//   W <- W - U (U^T W) twice, W = U_j R_j  (orthonormalisation below)
+//   Z = A^T U_j - V_j R_j^T
+//   Z <- Z - V (V^T Z) twice, Z = V_{j+1} S_{j+1}
+// so that A V = U T and A^T U = V T^T + V_{s+1} S_{s+1} E_s^T with T (ell x ell)
+// block upper bidiagonal: R_j on the diagonal, S_{j+1}^T above it.  The SVD
+// T = P Sigma Q^T gives Ritz triplets with residuals
+//   || A^T u_i - sigma_i v_i || = || S_{s+1} P[last b rows, i] ||.
+// A thick restart keeps k' Ritz vectors; T becomes diag(sigma_1..k') with the
+// spike block C = (S_{s+1} P[last b rows, 0:k'])^T in the columns of V_{s+1}.
+//
+// Orthonormalisation of a block X (len x b) against a basis: CGS2, then the
+// Gram matrix G = X^T X (FP32 products summed in FP64) is diagonalised in FP64
+// on the host (b x b Jacobi), X <- X Z Lambda^{-1/2}; directions with
+// Lambda_i <= 1e-8 Lambda_max (numerically dependent: a converged or exhausted
+// subspace) are replaced by fresh counter-based random vectors; then CGS2
+// again if any were replaced, and one Cholesky QR pass.  The factor R with
+// X_before = X_after R is accumulated in FP64.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "epilogue.cuh"
+#include "gkl_internal.cuh"
+
+namespace gkl {
+
+namespace {
+constexpr int kGramRows = 64;   // rows per FP32 partial sum
+constexpr int kMaxB = 32;       // block size limit (Gram kernel tile)
+}
+
+// ---- kernels ------------------------------------------------------------------
+
+// part[blk][i + p j] = sum over the block's rows r of X[r + i ldx] Y[r + j ldy]
+// (i < p <= 128, j < q <= 32): FP32 products over 64 rows, FP64 across.
+__global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ X, int64_t ldx, int p,
+                                                    const float* __restrict__ Y, int64_t ldy, int q, int64_t len,
+                                                    int64_t rows_per_blk, double* __restrict__ part) {
+    __shared__ float sx[kGramRows][129];
+    __shared__ float sy[kGramRows][33];
+    const int t = threadIdx.x, gi = t & 31, gj = t >> 5;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_blk;
+    const int64_t r1 = min(len, r0 + rows_per_blk);
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = 0.0;
+    for (int64_t rb = r0; rb < r1; rb += kGramRows) {
+        const int nr = (int)min((int64_t)kGramRows, r1 - rb);
+        for (int idx = t; idx < kGramRows * p; idx += 256) {
+            const int rr = idx % kGramRows, c = idx / kGramRows;
+            sx[rr][c] = rr < nr ? X[(rb + rr) + (int64_t)c * ldx] : 0.f;
+        }
+        for (int idx = t; idx < kGramRows * q; idx += 256) {
+            const int rr = idx % kGramRows, c = idx / kGramRows;
+            sy[rr][c] = rr < nr ? Y[(rb + rr) + (int64_t)c * ldy] : 0.f;
+        }
+        __syncthreads();
+        float f[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) f[a][c] = 0.f;
+        for (int rr = 0; rr < nr; ++rr) {
+            float xa[4], yc[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) xa[a] = (gi + 32 * a < p) ? sx[rr][gi + 32 * a] : 0.f;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) yc[c] = (gj + 8 * c < q) ? sy[rr][gj + 8 * c] : 0.f;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) f[a][c] = fmaf(xa[a], yc[c], f[a][c]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][c] += (double)f[a][c];
+        __syncthreads();
+    }
+    double* out = part + (int64_t)blockIdx.x * p * q;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int i = gi + 32 * a, j = gj + 8 * c;
+            if (i < p && j < q) out[i + p * j] = acc[a][c];
+        }
+}
+
+// out[e] = sum_blk part[blk][e] in block order (deterministic).
+__global__ void k_gram_sum(const double* __restrict__ part, int nblk, int pq, double* __restrict__ out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= pq) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * pq + e];
+    out[e] = s;
+}
+
+// X[:, 0:q] <- alpha X[:, 0:q] + beta Y[:, 0:p] C  (C p x q, FP64, column-major), per row.
+// X and Y may be the same buffer only with alpha = 0 (X <- beta X C).
+__global__ void __launch_bounds__(256) k_block_axpy(float* X, int64_t ldx, int q, const float* Y,
+                                                     int64_t ldy, int p, const double* __restrict__ C, float alpha,
+                                                     float beta, int64_t len) {
+    __shared__ float sc[128 * kMaxB];
+    for (int e = threadIdx.x; e < p * q; e += blockDim.x) sc[e] = (float)C[e];
+    __syncthreads();
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < len; r += (int64_t)gridDim.x * blockDim.x) {
+        float acc[kMaxB];
+#pragma unroll
+        for (int j = 0; j < kMaxB; ++j) acc[j] = 0.f;
+        for (int i = 0; i < p; ++i) {
+            const float y = Y[r + (int64_t)i * ldy];
+#pragma unroll
+            for (int j = 0; j < kMaxB; ++j)
+                if (j < q) acc[j] = fmaf(y, sc[i + p * j], acc[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < kMaxB; ++j)
+            if (j < q) {
+                float* x = X + r + (int64_t)j * ldx;
+                *x = (alpha == 0.f ? 0.f : alpha * *x) + beta * acc[j];
+            }
+    }
+}
+
+// X[:, j] <- uniform(-1, 1) from the counter-based generator, for the columns
+// flagged in `cols` (bit j).
+__global__ void k_block_random(float* __restrict__ X, int64_t ldx, int64_t len, uint32_t cols, uint64_t seed,
+                               uint32_t draw) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < len; r += (int64_t)gridDim.x * blockDim.x)
+        for (int j = 0; j < kMaxB; ++j)
+            if (cols & (1u << j)) X[r + (int64_t)j * ldx] = (float)uniform_pm1(seed, draw + (uint32_t)j, r);
+}
+
+// ---- host linear algebra (b x b, FP64) -----------------------------------------
+
+// Symmetric eigen-decomposition by cyclic Jacobi: G = Z diag(lam) Z^T.
+static void sym_eig(int q, std::vector<double> G, std::vector<double>& lam, std::vector<double>& Z) {
+    Z.assign((size_t)q * q, 0.0);
+    for (int i = 0; i < q; ++i) Z[i + q * i] = 1.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0, dia = 0.0;
+        for (int j = 0; j < q; ++j)
+            for (int i = 0; i < q; ++i) (i == j ? dia : off) += G[i + q * j] * G[i + q * j];
+        if (off <= 1e-30 * dia || off == 0.0) break;
+        for (int a = 0; a < q - 1; ++a)
+            for (int b = a + 1; b < q; ++b) {
+                const double gab = G[a + q * b];
+                if (gab == 0.0) continue;
+                const double zeta = (G[b + q * b] - G[a + q * a]) / (2.0 * gab);
+                const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / std::sqrt(1.0 + t * t), s = c * t;
+                for (int k = 0; k < q; ++k) {  // G <- J^T G J
+                    const double x = G[k + q * a], y = G[k + q * b];
+                    G[k + q * a] = c * x - s * y;
+                    G[k + q * b] = s * x + c * y;
+                }
+                for (int k = 0; k < q; ++k) {
+                    const double x = G[a + q * k], y = G[b + q * k];
+                    G[a + q * k] = c * x - s * y;
+                    G[b + q * k] = s * x + c * y;
+                }
+                for (int k = 0; k < q; ++k) {
+                    const double x = Z[k + q * a], y = Z[k + q * b];
+                    Z[k + q * a] = c * x - s * y;
+                    Z[k + q * b] = s * x + c * y;
+                }
+            }
+    }
+    lam.resize(q);
+    for (int i = 0; i < q; ++i) lam[i] = G[i + q * i];
+}
+
+// Cholesky G = R^T R (R upper, column-major); false if not positive definite.
+static bool cholesky(int q, const std::vector<double>& G, std::vector<double>& R) {
+    R.assign((size_t)q * q, 0.0);
+    for (int j = 0; j < q; ++j) {
+        double d = G[j + q * j];
+        for (int k = 0; k < j; ++k) d -= R[k + q * j] * R[k + q * j];
+        if (!(d > 0.0)) return false;
+        const double rjj = std::sqrt(d);
+        R[j + q * j] = rjj;
+        for (int i = j + 1; i < q; ++i) {
+            double s = G[j + q * i];
+            for (int k = 0; k < j; ++k) s -= R[k + q * j] * R[k + q * i];
+            R[j + q * i] = s / rjj;
+        }
+    }
+    return true;
+}
+
+// Inverse of an upper-triangular R (column-major).
+static std::vector<double> inv_upper(int q, const std::vector<double>& R) {
+    std::vector<double> X((size_t)q * q, 0.0);
+    for (int j = 0; j < q; ++j) {
+        X[j + q * j] = 1.0 / R[j + q * j];
+        for (int i = j - 1; i >= 0; --i) {
+            double s = 0.0;
+            for (int k = i + 1; k <= j; ++k) s += R[i + q * k] * X[k + q * j];
+            X[i + q * j] = -s / R[i + q * i];
+        }
+    }
+    return X;
+}
+
+static std::vector<double> matmul(int q, const std::vector<double>& A, const std::vector<double>& B) {
+    std::vector<double> C((size_t)q * q, 0.0);
+    for (int j = 0; j < q; ++j)
+        for (int k = 0; k < q; ++k) {
+            const double b = B[k + q * j];
+            if (b != 0.0)
+                for (int i = 0; i < q; ++i) C[i + q * j] += A[i + q * k] * b;
+        }
+    return C;
+}
+
+// ---- block driver -----------------------------------------------------------------
+
+struct BlockCtx {
+    gkl_handle* h;
+    cudaStream_t st;
+    double* d_part;    // Gram partials
+    double* d_small;   // p x q FP64 results / coefficient uploads
+    int nblk_max;
+    uint64_t seed;
+    uint32_t draw;
+    int launches;
+    int deflations;
+    double ms_mv, ms_rmv;
+    int64_t products;
+};
+
+static int gram_blocks(const BlockCtx& c, int64_t len) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>(c.nblk_max, (len + 1023) / 1024));
+}
+
+// C (p x q, device FP64) = X^T Y
+static cudaError_t gram(BlockCtx& c, const float* X, int64_t ldx, int p, const float* Y, int64_t ldy, int q,
+                        int64_t len, double* C) {
+    const int nb = gram_blocks(c, len);
+    const int64_t rpb = (len + nb - 1) / nb;
+    k_gram_part<<<nb, 256, 0, c.st>>>(X, ldx, p, Y, ldy, q, len, rpb, c.d_part);
+    k_gram_sum<<<(p * q + 255) / 256, 256, 0, c.st>>>(c.d_part, nb, p * q, C);
+    c.launches += 2;
+    return cudaGetLastError();
+}
+
+static int axpy_grid(const BlockCtx& c, int64_t len) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>(4 * c.h->num_sms, (len + 255) / 256));
+}
+
+// X <- X - B (B^T X) twice, B = len x nb basis
+static cudaError_t cgs2(BlockCtx& c, float* X, int64_t ldx, int q, const float* B, int64_t ldb, int nbasis,
+                        int64_t len) {
+    if (nbasis == 0) return cudaSuccess;
+    for (int pass = 0; pass < 2; ++pass) {
+        cudaError_t e = gram(c, B, ldb, nbasis, X, ldx, q, len, c.d_small);
+        if (e != cudaSuccess) return e;
+        k_block_axpy<<<axpy_grid(c, len), 256, 0, c.st>>>(X, ldx, q, B, ldb, nbasis, c.d_small, 1.f, -1.f, len);
+        c.launches += 1;
+    }
+    return cudaGetLastError();
+}
+
+
+static cudaError_t upload(BlockCtx& c, const std::vector<double>& hm, double* dst) {
+    return cudaMemcpyAsync(dst, hm.data(), sizeof(double) * hm.size(), cudaMemcpyHostToDevice, c.st);
+}
+
+static cudaError_t download(BlockCtx& c, const double* src, std::vector<double>& hm, size_t count) {
+    hm.resize(count);
+    cudaError_t e = cudaMemcpyAsync(hm.data(), src, sizeof(double) * count, cudaMemcpyDeviceToHost, c.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
+    return e;
+}
+
+// Orthonormalise X (len x q) against B (len x nb); returns R (q x q, column-major)
+// with X_before = X_after R (up to the replaced directions, whose rows of R are 0).
+static cudaError_t orthonormalize(BlockCtx& c, float* X, int64_t ldx, int q, const float* B, int64_t ldb, int nb,
+                                  int64_t len, std::vector<double>& R) {
+    cudaError_t e = cgs2(c, X, ldx, q, B, ldb, nb, len);
+    std::vector<double> G, lam, Z;
+    if (e == cudaSuccess) e = gram(c, X, ldx, q, X, ldx, q, len, c.d_small);
+    if (e == cudaSuccess) e = download(c, c.d_small, G, (size_t)q * q);
+    if (e != cudaSuccess) return e;
+    sym_eig(q, G, lam, Z);
+    // descending eigenvalues, so that replaced directions come last
+    std::vector<int> ord(q);
+    for (int i = 0; i < q; ++i) ord[i] = i;
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) { return lam[a] > lam[b]; });
+    const double lmax = std::max(0.0, lam[ord[0]]);
+    std::vector<double> M((size_t)q * q, 0.0), R1((size_t)q * q, 0.0);
+    uint32_t repl = 0;
+    for (int jj = 0; jj < q; ++jj) {
+        const int i = ord[jj];
+        if (lmax > 0.0 && lam[i] > 1e-8 * lmax) {
+            const double sl = std::sqrt(lam[i]);
+            for (int r = 0; r < q; ++r) {
+                M[r + q * jj] = Z[r + q * i] / sl;
+                R1[jj + q * r] = sl * Z[r + q * i];
+            }
+        } else {
+            repl |= 1u << jj;
+        }
+    }
+    e = upload(c, M, c.d_small);
+    if (e != cudaSuccess) return e;
+    k_block_axpy<<<axpy_grid(c, len), 256, 0, c.st>>>(X, ldx, q, X, ldx, q, c.d_small, 0.f, 1.f, len);
+    c.launches += 1;
+    if (repl) {
+        k_block_random<<<axpy_grid(c, len), 256, 0, c.st>>>(X, ldx, len, repl, c.seed, c.draw);
+        c.draw += kMaxB;
+        c.launches += 1;
+        c.deflations += __builtin_popcount(repl);
+        e = cgs2(c, X, ldx, q, B, ldb, nb, len);
+        if (e != cudaSuccess) return e;
+    }
+    // one Cholesky QR pass on the (now well-conditioned) block
+    if ((e = gram(c, X, ldx, q, X, ldx, q, len, c.d_small)) != cudaSuccess) return e;
+    if ((e = download(c, c.d_small, G, (size_t)q * q)) != cudaSuccess) return e;
+    std::vector<double> R2;
+    if (!cholesky(q, G, R2)) return cudaErrorInvalidValue;
+    const std::vector<double> R2i = inv_upper(q, R2);
+    if ((e = upload(c, R2i, c.d_small)) != cudaSuccess) return e;
+    k_block_axpy<<<axpy_grid(c, len), 256, 0, c.st>>>(X, ldx, q, X, ldx, q, c.d_small, 0.f, 1.f, len);
+    c.launches += 1;
+    R = matmul(q, R2, R1);
+    return cudaGetLastError();
+}
+
+// Y[:, 0:q] = A X[:, 0:q] (forward) or A^T X (transpose), one column at a time
+// with the single-vector kernels.
+static cudaError_t block_product(BlockCtx& c, bool transpose, const float* X, int64_t ldx, float* Y, int64_t ldy,
+                                 int q) {
+    gkl_handle* h = c.h;
+    for (int j = 0; j < q; ++j) {
+        int nl = 0;
+        cudaError_t e = transpose ? launch_rmatvec<float>(h, X + (int64_t)j * ldx, Y + (int64_t)j * ldy, h->scratch,
+                                                          nullptr, nullptr, nullptr, nullptr, &nl)
+                                  : launch_matvec<float>(h, X + (int64_t)j * ldx, Y + (int64_t)j * ldy, h->scratch,
+                                                         nullptr, nullptr, nullptr, nullptr, &nl);
+        if (e != cudaSuccess) return e;
+        c.launches += nl;
+    }
+    c.products += transpose ? 0 : q;
+    return cudaSuccess;
+}
+
+static int64_t round32(int64_t x) { return (x + 31) / 32 * 32; }
+
+int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, float* Vout, double* resid,
+              gkl_info* info) {
+    const int64_t n = h->n, m = h->m;
+    const int b = o->block ? o->block : 32;
+    const int k = o->k;
+    if (b < 1 || b > kMaxB) return set_err(h, GKL_ERR_ARG, "block size %d outside [1, %d]", b, kMaxB);
+    const int ell = o->ell / b * b;
+    if (k < 1 || ell < 2 * b || ell > GKL_MAX_ELL || k >= ell || ell > std::min(n, m))
+        return set_err(h, GKL_ERR_ARG, "need 1 <= k < ell, 2b <= ell <= min(n, m, %d) (ell rounded down to a multiple of b)",
+                       GKL_MAX_ELL);
+    int kk = o->k_keep;
+    if (kk == 0) kk = std::max(k, ell - b * (int)((ell - k + 2 * b - 1) / (2 * b)));
+    if (kk < k || kk >= ell || (ell - kk) % b != 0)
+        return set_err(h, GKL_ERR_ARG, "k_keep must satisfy k <= k_keep < ell with ell - k_keep a multiple of b");
+    if (!(o->tol > 0.0) || o->maxit < 1) return set_err(h, GKL_ERR_ARG, "tol must be > 0 and maxit >= 1");
+    MvPlan plan = plan_products(h);
+    int st = ensure_scratch(h, plan.bytes_fp64);
+    if (st) return st;
+    const int64_t ldu = round32(n), ldv = round32(m);
+    const size_t ell2 = (size_t)ell * ell;
+    const int nblk = 4 * h->num_sms;
+    // device workspace
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o2 = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o2;
+    };
+    const size_t oU = take(sizeof(float) * ldu * ell), oU2 = take(sizeof(float) * ldu * ell);
+    const size_t oV = take(sizeof(float) * ldv * (ell + b)), oV2 = take(sizeof(float) * ldv * (ell + b));
+    const size_t oT = take(sizeof(double) * ell2), oP = take(sizeof(double) * 4 * ell2),
+                 oQ = take(sizeof(double) * ell2), oRw = take(sizeof(double) * 8 * ell2);
+    const size_t oSc = take(sizeof(DevScal)), oCo = take(sizeof(CycleOut));
+    const size_t oPart = take(sizeof(double) * (size_t)nblk * GKL_MAX_ELL * kMaxB),
+                 oSmall = take(sizeof(double) * GKL_MAX_ELL * kMaxB), oSigns = take(sizeof(int) * GKL_MAX_ELL);
+    const size_t oOutU = take(sizeof(float) * n * k), oOutV = take(sizeof(float) * m * k);
+    void* ws = nullptr;
+    if (cudaMalloc(&ws, off) != cudaSuccess) return set_err(h, GKL_ERR_CUDA, "block workspace of %zu bytes", off);
+    char* W = static_cast<char*>(ws);
+    float* U = reinterpret_cast<float*>(W + oU);
+    float* U2 = reinterpret_cast<float*>(W + oU2);
+    float* V = reinterpret_cast<float*>(W + oV);
+    float* V2 = reinterpret_cast<float*>(W + oV2);
+    Sv sv{};
+    sv.n = n;
+    sv.m = m;
+    sv.ldu = ldu;
+    sv.ldv = ldv;
+    sv.ell = ell;
+    sv.kk = kk;
+    sv.k = k;
+    sv.prec = GKL_FP32;
+    sv.B = reinterpret_cast<double*>(W + oT);
+    sv.P = reinterpret_cast<double*>(W + oP);
+    sv.Q = reinterpret_cast<double*>(W + oQ);
+    sv.rw = reinterpret_cast<double*>(W + oRw);
+    sv.sc = reinterpret_cast<DevScal*>(W + oSc);
+    sv.co = reinterpret_cast<CycleOut*>(W + oCo);
+    sv.eps_w = 5.9604644775390625e-08;
+    sv.tol = o->tol;
+    BlockCtx c{h, h->stream, reinterpret_cast<double*>(W + oPart), reinterpret_cast<double*>(W + oSmall), nblk,
+               o->seed, 0x42000000u, 0, 0, 0.0, 0.0, 0};
+    cudaError_t e = cudaMemsetAsync(sv.sc, 0, sizeof(DevScal), c.st);
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    cudaEventRecord(ev0, c.st);
+    std::vector<double> T(ell2, 0.0), R, S, P, sg;
+    std::vector<double> Slast;
+    CycleOut* ho = h->host_out;
+    int cycle = 0, restarts = 0, converged = 0;
+    double maxrel = 0.0, dtheta = 0.0;
+    std::vector<double> res(k, 0.0);
+    auto fail = [&](const char* what) {
+        cudaFree(ws);
+        cudaEventDestroy(ev0);
+        cudaEventDestroy(ev1);
+        return e != cudaSuccess ? cuda_err(h, e, what) : set_err(h, GKL_ERR_CUDA, "%s", what);
+    };
+    // start block: V[:, 0:b] random (or v0 in column 0), orthonormalised
+    if (e == cudaSuccess) {
+        k_block_random<<<axpy_grid(c, m), 256, 0, c.st>>>(V, ldv, m, b == 32 ? 0xFFFFFFFFu : ((1u << b) - 1u), c.seed,
+                                                          c.draw);
+        c.draw += kMaxB;
+        if (o->v0) e = cudaMemcpyAsync(V, o->v0, sizeof(float) * m, cudaMemcpyDeviceToDevice, c.st);
+    }
+    if (e == cudaSuccess) e = orthonormalize(c, V, ldv, b, nullptr, ldv, 0, m, R);
+    if (e != cudaSuccess) return fail("block start");
+    for (cycle = 0; cycle < o->maxit; ++cycle) {
+        const int c0 = cycle == 0 ? 0 : kk;
+        for (int j0 = c0; j0 < ell; j0 += b) {
+            float* Wb = U + (int64_t)j0 * ldu;
+            cudaEventRecord(ev1, c.st);
+            if ((e = block_product(c, false, V + (int64_t)j0 * ldv, ldv, Wb, ldu, b)) != cudaSuccess)
+                return fail("A V block");
+            if (j0 > 0) {  // W -= U[:, 0:j0] T[0:j0, j0:j0+b]
+                std::vector<double> Cs((size_t)j0 * b);
+                for (int cc = 0; cc < b; ++cc)
+                    for (int r = 0; r < j0; ++r) Cs[r + (size_t)j0 * cc] = T[r + (size_t)ell * (j0 + cc)];
+                if ((e = upload(c, Cs, c.d_small)) != cudaSuccess) return fail("coupling upload");
+                k_block_axpy<<<axpy_grid(c, n), 256, 0, c.st>>>(Wb, ldu, b, U, ldu, j0, c.d_small, 1.f, -1.f, n);
+                c.launches += 1;
+            }
+            if ((e = orthonormalize(c, Wb, ldu, b, U, ldu, j0, n, R)) != cudaSuccess) return fail("U block");
+            for (int cc = 0; cc < b; ++cc)
+                for (int r = 0; r < b; ++r) T[(j0 + r) + (size_t)ell * (j0 + cc)] = R[r + (size_t)b * cc];
+            float* Zb = V + (int64_t)(j0 + b) * ldv;
+            if ((e = block_product(c, true, Wb, ldu, Zb, ldv, b)) != cudaSuccess) return fail("A^T U block");
+            {  // Z -= V[:, j0:j0+b] R^T
+                std::vector<double> Rt((size_t)b * b);
+                for (int i = 0; i < b; ++i)
+                    for (int jj = 0; jj < b; ++jj) Rt[i + (size_t)b * jj] = R[jj + (size_t)b * i];
+                if ((e = upload(c, Rt, c.d_small)) != cudaSuccess) return fail("R upload");
+                k_block_axpy<<<axpy_grid(c, m), 256, 0, c.st>>>(Zb, ldv, b, V + (int64_t)j0 * ldv, ldv, b,
+                                                               c.d_small, 1.f, -1.f, m);
+                c.launches += 1;
+            }
+            if ((e = orthonormalize(c, Zb, ldv, b, V, ldv, j0 + b, m, S)) != cudaSuccess) return fail("V block");
+            if (j0 + b < ell) {
+                for (int cc = 0; cc < b; ++cc)
+                    for (int r = 0; r < b; ++r) T[(j0 + r) + (size_t)ell * (j0 + b + cc)] = S[cc + (size_t)b * r];
+            } else {
+                Slast = S;
+            }
+        }
+        // projected SVD of T (FP32 Jacobi + FP64 refinement, FP64 fallback)
+        if ((e = upload(c, T, sv.B)) != cudaSuccess) return fail("T upload");
+        if ((e = launch_small_svd(sv, c.st, 0)) != cudaSuccess) return fail("projected SVD");
+        c.launches += 10;
+        e = cudaMemcpyAsync(ho, sv.co, sizeof(CycleOut), cudaMemcpyDeviceToHost, c.st);
+        if (e == cudaSuccess) e = download(c, sv.P, P, ell2);
+        if (e != cudaSuccess) return fail("projected SVD results");
+        sg.assign(ho->sg, ho->sg + ell);
+        // block residuals r_i = || S_last P[ell-b:ell, i] ||
+        double mx = 0.0, sum = 0.0;
+        std::vector<double> SP((size_t)b * ell);
+        for (int i = 0; i < ell; ++i)
+            for (int r = 0; r < b; ++r) {
+                double a = 0.0;
+                for (int t = 0; t < b; ++t) a += Slast[r + (size_t)b * t] * P[(ell - b + t) + (size_t)ell * i];
+                SP[r + (size_t)b * i] = a;
+            }
+        for (int i = 0; i < k; ++i) {
+            double a = 0.0;
+            for (int r = 0; r < b; ++r) a += SP[r + (size_t)b * i] * SP[r + (size_t)b * i];
+            res[i] = std::sqrt(a);
+            mx = std::max(mx, res[i]);
+            sum += res[i];
+        }
+        maxrel = sg[0] > 0.0 ? mx / sg[0] : 0.0;
+        dtheta = sum;
+        converged = mx <= o->tol * sg[0] || sg[0] == 0.0;
+        if (converged || cycle == o->maxit - 1) break;
+        // thick restart: keep kk Ritz vectors, spike block from S_last
+        e = launch_rotate<float>(c.st, U, ldu, ell, sv.P, ell, kk, U2, ldu, n);
+        if (e == cudaSuccess) e = launch_rotate<float>(c.st, V, ldv, ell, sv.Q, ell, kk, V2, ldv, m);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(V2 + (int64_t)kk * ldv, sizeof(float) * ldv, V + (int64_t)ell * ldv,
+                                  sizeof(float) * ldv, sizeof(float) * m, b, cudaMemcpyDeviceToDevice, c.st);
+        if (e != cudaSuccess) return fail("restart");
+        c.launches += 2;
+        std::swap(U, U2);
+        std::swap(V, V2);
+        std::fill(T.begin(), T.end(), 0.0);
+        for (int i = 0; i < kk; ++i) {
+            T[i + (size_t)ell * i] = sg[i];
+            for (int cc = 0; cc < b; ++cc) T[i + (size_t)ell * (kk + cc)] = SP[cc + (size_t)b * i];
+        }
+        ++restarts;
+    }
+    // output: U P[:, :k], V Q[:, :k], sign rule, copy-out
+    float* Uo = reinterpret_cast<float*>(W + oOutU);
+    float* Vo = reinterpret_cast<float*>(W + oOutV);
+    e = launch_rotate<float>(c.st, U, ldu, ell, sv.P, ell, k, Uo, n, n);
+    if (e == cudaSuccess) e = launch_rotate<float>(c.st, V, ldv, ell, sv.Q, ell, k, Vo, m, m);
+    if (e == cudaSuccess) e = launch_sign_fix<float>(c.st, Uo, n, Vo, m, k, reinterpret_cast<int*>(W + oSigns));
+    if (e == cudaSuccess && Uout) e = cudaMemcpyAsync(Uout, Uo, sizeof(float) * n * k, cudaMemcpyDeviceToDevice, c.st);
+    if (e == cudaSuccess && Vout) e = cudaMemcpyAsync(Vout, Vo, sizeof(float) * m * k, cudaMemcpyDeviceToDevice, c.st);
+    cudaEventRecord(ev1, c.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
+    if (e != cudaSuccess) return fail("output");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    for (int i = 0; i < k; ++i) {
+        sigma[i] = sg[i];
+        if (resid) resid[i] = res[i];
+    }
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        info->matvec_pairs = c.products;
+        info->restarts = restarts;
+        info->cycles = cycle + 1;
+        info->breakdowns = c.deflations;
+        info->converged = converged;
+        info->max_rel_resid = maxrel;
+        info->dtheta1 = dtheta;
+        info->ms_total = ms;
+        info->launches = c.launches + 5;
+    }
+    h->last_valid = 0;  // gkl_grad works from the single-vector solvers' triplets
+    cudaFree(ws);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    return converged ? GKL_OK : GKL_NOT_CONVERGED;
+}
+
+}  // namespace gkl

@@ -256,6 +256,9 @@ __device__ inline void step_epilogue(const Sv& sv, int role, int j, double nrm2)
         }
         reset_estimates(sv.nuh, L, j + 1, j + 1, sv.eps_w);
         break;
+    case ROLE_STORE:
+        if (threadIdx.x == 0) sc->pre = nrm2;
+        break;
     default:
         break;
     }

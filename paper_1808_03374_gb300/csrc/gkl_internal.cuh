@@ -88,6 +88,18 @@ struct gkl_handle {
     size_t ws_bytes;
     gkl::CycleOut* host_out;  // pinned
     double* aux;     // small zero-initialised device buffer: scale/sum of the tensor-core product + its counter
+    // triplets of the last successful gkl_svd (for gkl_grad)
+    int last_valid, last_prec, last_k;
+    double last_sigma[GKL_MAX_ELL];
+    double last_next;  // Ritz value k+1 of the last cycle (estimate of sigma_{k+1})
+    void* last_U;      // n x k, precision's type
+    void* last_V;      // m x k
+    size_t last_bytes;
+    void* gws;         // gradient workspace (grown on demand)
+    size_t gws_bytes;
+    // tensor-core (tcgen05) A^T u: 0 = not prepared, 1 = ready, -1 = unavailable or disabled
+    int tc_state;
+    alignas(64) unsigned char tc_map[128];  // TMA descriptor of the packed matrix
     char err[512];
 };
 
@@ -132,6 +144,18 @@ size_t rmv_mma_scratch_bytes(const gkl_handle* h);
 cudaError_t launch_rmatvec_mma(const gkl_handle* h, const float* u, float* x, void* scratch, const Sv* sv,
                                const FinArgs* fa, cudaEvent_t ev0, cudaEvent_t ev1, int* nlaunch);
 constexpr size_t kAuxBytes = 64 * 1024;
+constexpr size_t kAuxErrOffset = 60 * 1024;  // int: nonzero if a tensor-core kernel's wait ran out
+// Shared by the two tensor-core A^T u paths (defined in packed_mma.cu).
+__global__ void __launch_bounds__(256) k_u_scale(const float* u, const float* s, int64_t n, double* part,
+                                                  unsigned* counter, double* dsc);
+__global__ void __launch_bounds__(256) k_rmv_mma_fin(const double* p1, const double* p3, int nb, int64_t m,
+                                                      const double* mu, const double* d, const float* w,
+                                                      const double* dsc, float* x, FinArgs fa, Sv sv);
+// tcgen05 A^T u (FP32 path, packed_tc.cu); tc_prepare builds the TMA descriptor once per handle.
+bool tc_prepare(gkl_handle* h);
+size_t rmv_tc_scratch_bytes(const gkl_handle* h);
+cudaError_t launch_rmatvec_tc(const gkl_handle* h, const float* u, float* x, void* scratch, const Sv* sv,
+                              const FinArgs* fa, cudaEvent_t ev0, cudaEvent_t ev1, int* nlaunch);
 
 cudaError_t launch_colstats(const uint8_t* packed, int64_t n, int64_t m, int64_t stride, double* mu, double* scale,
                             int64_t* nobs, cudaStream_t st);
@@ -145,7 +169,8 @@ enum {
     ROLE_V_POST = 4,
     ROLE_START = 5,
     ROLE_REPL_U = 6,
-    ROLE_REPL_V = 7
+    ROLE_REPL_V = 7,
+    ROLE_STORE = 8  // keep ||x||^2 in DevScal::pre (gradient solves)
 };
 enum { CGS_DOTS = 0, CGS_UPD_DOTS = 1, CGS_UPD_NORM = 2, CGS_FILL_DOTS = 3 };
 int cgs_grid(int64_t len, int num_sms);
@@ -163,6 +188,9 @@ cudaError_t launch_rotate(cudaStream_t st, const T* in, int64_t ldin, int ell, c
 template <typename T>
 cudaError_t launch_sign_fix(cudaStream_t st, T* U, int64_t n, T* V, int64_t m, int k, int* signs);
 cudaError_t launch_small_svd(const Sv& sv, cudaStream_t st, int restart_ready);
+// block form (block.cu)
+int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, float* Vout, double* resid,
+              gkl_info* info);
 cudaError_t launch_init_state(const Sv& sv, cudaStream_t st);
 
 // ---- Philox4x32-10 (Salmon et al., SC'11) for the start vector and breakdown restarts

@@ -87,7 +87,9 @@ MvPlan plan_products(const gkl_handle* h) {
     p.ldp = p.nwords * 16;
     size_t mv = (size_t)p.chunks * (size_t)p.ldp + (size_t)h->m * 4;  // partials + LUT
     size_t rmv = 2 * (size_t)p.tiles * (size_t)h->m;
-    p.bytes_fp64 = std::max(std::max(mv, rmv) * sizeof(double) + 256, h->aux ? rmv_mma_scratch_bytes(h) : 0);
+    size_t tc = h->aux ? rmv_mma_scratch_bytes(h) : 0;
+    if (h->tc_state > 0) tc = std::max(tc, rmv_tc_scratch_bytes(h));
+    p.bytes_fp64 = std::max(std::max(mv, rmv) * sizeof(double) + 256, tc);
     return p;
 }
 
@@ -168,6 +170,8 @@ __global__ void __launch_bounds__(kThreads) k_mv_pair(const uint8_t* __restrict_
                                                       const float* __restrict__ lut, float* __restrict__ part,
                                                       int64_t ldp) {
     __shared__ float tab[kPairBatch * 16];
+    __shared__ __align__(16) float lrow[2 * kPairBatch * 4];
+    static_assert(2 * kPairBatch * 4 == 2 * kThreads, "one float2 of per-SNP table rows per thread");
     const int64_t word = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     const int64_t j0 = (int64_t)blockIdx.y * rpc;
     const int64_t j1 = min(m, j0 + (int64_t)rpc);
@@ -177,51 +181,75 @@ __global__ void __launch_bounds__(kThreads) k_mv_pair(const uint8_t* __restrict_
     float acc[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) acc[k] = 0.f;
-    for (int64_t jb = j0; jb < j1; jb += 2 * kPairBatch) {
-        const int nrows = (int)min((int64_t)(2 * kPairBatch), j1 - jb);
+    // per-SNP table rows of a batch: thread t holds floats 2t, 2t+1 (row t/2)
+    auto fetch_rows = [&](int64_t jb, int nrows) -> float2 {
+        const int r = threadIdx.x >> 1;
+        return r < nrows ? *reinterpret_cast<const float2*>(lut + jb * 4 + 2 * threadIdx.x) : make_float2(0.f, 0.f);
+    };
+    auto load_group = [&](int64_t jb, int nrows, int p0, uint32_t (&xa)[4], uint32_t (&xb)[4]) {
+        const uint32_t* rp = base + (jb + 2 * p0) * wstride;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int ra = 2 * (p0 + q), rb = ra + 1;
+            xa[q] = (ra < nrows) ? __ldg(rp + (2 * q) * wstride) : 0xFFFFFFFFu;
+            xb[q] = (rb < nrows) ? __ldg(rp + (2 * q + 1) * wstride) : 0xFFFFFFFFu;
+        }
+    };
+    // The next batch's table rows and first group of code words are fetched
+    // before the current batch is consumed, so the barriers that rebuild the
+    // pair tables do not drain the memory pipeline.
+    uint32_t wa[4], wb[4], na[4], nb[4];
+    int64_t jb = j0;
+    int nrows = (int)min((int64_t)(2 * kPairBatch), j1 - jb);
+    float2 lcur = fetch_rows(jb, nrows);
+    if (active && nrows > 0) load_group(jb, nrows, 0, wa, wb);
+    while (jb < j1) {
         const int npairs = (nrows + 1) >> 1;
+        __syncthreads();
+        *reinterpret_cast<float2*>(lrow + 2 * threadIdx.x) = lcur;
         __syncthreads();
         for (int e = threadIdx.x; e < npairs * 16; e += kThreads) {
             const int p = e >> 4, ca = e & 3, cb = (e >> 2) & 3;
             const int ra = 2 * p, rb = 2 * p + 1;
-            float va = lut[(jb + ra) * 4 + ca];
-            float vb = rb < nrows ? lut[(jb + rb) * 4 + cb] : 0.f;
-            tab[e] = va + vb;
+            tab[e] = lrow[ra * 4 + ca] + (rb < nrows ? lrow[rb * 4 + cb] : 0.f);
         }
         __syncthreads();
-        if (!active) continue;
-        // two groups of four row pairs in flight: load group p0+4 while group p0 is used
-        uint32_t wa[4], wb[4], na[4], nb[4];
-        auto load_group = [&](int p0, uint32_t (&xa)[4], uint32_t (&xb)[4]) {
-            const uint32_t* rp = base + (jb + 2 * p0) * wstride;
+        const int64_t jn = jb + 2 * kPairBatch;
+        const int nrn = jn < j1 ? (int)min((int64_t)(2 * kPairBatch), j1 - jn) : 0;
+        if (nrn > 0) lcur = fetch_rows(jn, nrn);
+        if (active) {
+            for (int p0 = 0; p0 < npairs; p0 += 4) {
+                if (p0 + 4 < npairs) load_group(jb, nrows, p0 + 4, na, nb);
+                else if (nrn > 0) load_group(jn, nrn, 0, na, nb);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int ra = 2 * (p0 + q), rb = ra + 1;
-                xa[q] = (ra < nrows) ? __ldg(rp + (2 * q) * wstride) : 0xFFFFFFFFu;
-                xb[q] = (rb < nrows) ? __ldg(rp + (2 * q + 1) * wstride) : 0xFFFFFFFFu;
-            }
-        };
-        load_group(0, wa, wb);
-        for (int p0 = 0; p0 < npairs; p0 += 4) {
-            if (p0 + 4 < npairs) load_group(p0 + 4, na, nb);
+                for (int q = 0; q < 4; ++q) {
+                    if (p0 + q >= npairs) break;
+                    const char* T = reinterpret_cast<const char*>(tab + (p0 + q) * 16);
+                    const uint32_t e = (wa[q] & 0x33333333u) | ((wb[q] & 0x33333333u) << 2);
+                    const uint32_t o = ((wa[q] >> 2) & 0x33333333u) | (wb[q] & 0xCCCCCCCCu);
+                    // byte offsets 4 * index: bytes of eL hold nibbles 0, 2, 4, 6 of e (samples
+                    // 0, 4, 8, 12), bytes of eH nibbles 1, 3, 5, 7 (samples 2, 6, 10, 14); likewise
+                    // for o (odd samples).  One byte-permute then yields each offset.
+                    const uint32_t eL = (e << 2) & 0x3C3C3C3Cu, eH = (e >> 2) & 0x3C3C3C3Cu;
+                    const uint32_t oL = (o << 2) & 0x3C3C3C3Cu, oH = (o >> 2) & 0x3C3C3C3Cu;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (p0 + q >= npairs) break;
-                const float* T = tab + (p0 + q) * 16;
-                const uint32_t e = (wa[q] & 0x33333333u) | ((wb[q] & 0x33333333u) << 2);
-                const uint32_t o = ((wa[q] >> 2) & 0x33333333u) | (wb[q] & 0xCCCCCCCCu);
+                    for (int b = 0; b < 4; ++b) {
+                        const uint32_t sel = 0x4440u | (uint32_t)b;
+                        acc[4 * b] += *reinterpret_cast<const float*>(T + __byte_perm(eL, 0u, sel));
+                        acc[4 * b + 1] += *reinterpret_cast<const float*>(T + __byte_perm(oL, 0u, sel));
+                        acc[4 * b + 2] += *reinterpret_cast<const float*>(T + __byte_perm(eH, 0u, sel));
+                        acc[4 * b + 3] += *reinterpret_cast<const float*>(T + __byte_perm(oH, 0u, sel));
+                    }
+                }
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    acc[2 * k] += T[(e >> (4 * k)) & 15u];
-                    acc[2 * k + 1] += T[(o >> (4 * k)) & 15u];
+                for (int q = 0; q < 4; ++q) {
+                    wa[q] = na[q];
+                    wb[q] = nb[q];
                 }
             }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                wa[q] = na[q];
-                wb[q] = nb[q];
-            }
         }
+        jb = jn;
+        nrows = nrn;
     }
     if (!active) return;
     float4* out = reinterpret_cast<float4*>(part + (int64_t)blockIdx.y * ldp + word * 16);
@@ -427,6 +455,9 @@ template <typename T>
 cudaError_t launch_rmatvec(const gkl_handle* h, const T* u, T* x, void* scratch, const Sv* sv, const FinArgs* fa,
                            cudaEvent_t ev0, cudaEvent_t ev1, int* nlaunch) {
     if constexpr (sizeof(T) == sizeof(float)) {
+        if (h->aux && h->tc_state > 0)
+            return launch_rmatvec_tc(h, reinterpret_cast<const float*>(u), reinterpret_cast<float*>(x), scratch, sv,
+                                     fa, ev0, ev1, nlaunch);
         if (h->aux)
             return launch_rmatvec_mma(h, reinterpret_cast<const float*>(u), reinterpret_cast<float*>(x), scratch, sv,
                                       fa, ev0, ev1, nlaunch);

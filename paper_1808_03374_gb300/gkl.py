@@ -16,16 +16,17 @@ import torch
 
 from .build import LIB as _LIB_PATH
 
-FP64, FP32 = 0, 1
+FP64, FP32, BLOCK = 0, 1, 2
 REORTH_FULL, REORTH_PARTIAL = 0, 1
 OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, NOT_CONVERGED, ERR_GAP, ERR_STATE = range(7)
 
-_PREC = {"fp64": FP64, "fp32": FP32}
+_PREC = {"fp64": FP64, "fp32": FP32, "block": BLOCK}
 _REORTH = {"full": REORTH_FULL, "partial": REORTH_PARTIAL}
-_DTYPE = {FP64: torch.float64, FP32: torch.float32}
+_DTYPE = {FP64: torch.float64, FP32: torch.float32, BLOCK: torch.float32}
 
 EXPORTS = ["gkl_version", "gkl_last_error", "gkl_opts_default", "gkl_colstats", "gkl_init", "gkl_set_stream",
-           "gkl_set_weights", "gkl_matvec", "gkl_rmatvec", "gkl_svd", "gkl_destroy", "gkl_matvec_noalloc"]
+           "gkl_set_weights", "gkl_matvec", "gkl_rmatvec", "gkl_svd", "gkl_destroy", "gkl_matvec_noalloc",
+           "gkl_grad"]
 
 
 class GKLError(RuntimeError):
@@ -37,7 +38,7 @@ class GKLError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("ell", ctypes.c_int32), ("k_keep", ctypes.c_int32),
                 ("reorth", ctypes.c_int32), ("precision", ctypes.c_int32), ("maxit", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32), ("tol", ctypes.c_double), ("omega", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("profile", ctypes.c_int32), ("block", ctypes.c_int32), ("tol", ctypes.c_double), ("omega", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("v0", ctypes.c_void_p)]
 
 
@@ -79,6 +80,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.gkl_svd.argtypes = [vp, ctypes.POINTER(Opts), vp, vp, vp, vp, ctypes.POINTER(Info)]
     lib.gkl_destroy.argtypes = [vp]
     lib.gkl_matvec_noalloc.argtypes = [vp, i64, i64, i64, vp, vp, i32, vp, vp, vp]
+    lib.gkl_grad.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double]
+    lib.gkl_grad.restype = ctypes.c_int
     for f in ("gkl_colstats", "gkl_init", "gkl_set_stream", "gkl_set_weights", "gkl_matvec", "gkl_rmatvec",
               "gkl_svd", "gkl_destroy", "gkl_matvec_noalloc"):
         getattr(lib, f).restype = ctypes.c_int
@@ -193,13 +196,15 @@ class GKL:
     def svd(self, k: int, ell: int, reorth: str = "full", precision: str = "fp64", tol: float = 1e-10,
             maxit: int = 1000, k_keep: int = 0, omega: float = 0.0, seed: int = 1,
             v0: torch.Tensor | None = None, want_u: bool = True, want_v: bool = True, profile: bool = False,
-            U: torch.Tensor | None = None, V: torch.Tensor | None = None, raise_on_fail: bool = True) -> SVDResult:
+            U: torch.Tensor | None = None, V: torch.Tensor | None = None, raise_on_fail: bool = True,
+            block: int = 0) -> SVDResult:
         prec = _PREC[precision]
         dt = _DTYPE[prec]
         o = Opts()
         lib().gkl_opts_default(ctypes.byref(o))
         o.k, o.ell, o.k_keep, o.reorth, o.precision, o.maxit = k, ell, k_keep, _REORTH[reorth], prec, maxit
         o.tol, o.omega, o.seed, o.profile = tol, omega, seed, int(profile)
+        o.block = block
         if v0 is not None:
             v0 = v0.to(self.device, dt).contiguous()
             o.v0 = v0.data_ptr()
@@ -216,3 +221,51 @@ class GKL:
         if st not in (OK, NOT_CONVERGED) and raise_on_fail:
             _check(st, self._h)
         return SVDResult(sigma, None if U is None else U.T, None if V is None else V.T, resid, info.as_dict(), st)
+
+    def grad(self, sigma_bar=None, scores_bar: torch.Tensor | None = None, want_w: bool = True,
+             want_s: bool = True, min_relgap: float = 1e-3, dtype=torch.float64):
+        """(dL/ds, dL/dw) for the triplets of the last converged svd() call.
+
+        sigma_bar: k adjoints of the singular values; scores_bar: n x k
+        adjoints of the PC scores U diag(sigma).  dtype must be the precision
+        of that solve."""
+        sb = None
+        if sigma_bar is not None:
+            sb = np.ascontiguousarray(np.asarray(sigma_bar, dtype=np.float64))
+        Sb = None
+        if scores_bar is not None:
+            Sb = scores_bar.to(self.device, dtype).t().contiguous()  # column-major n x k
+        gw = torch.empty(self.m, dtype=dtype, device=self.device) if want_w else None
+        gs = torch.empty(self.n, dtype=dtype, device=self.device) if want_s else None
+        self._sync_stream()
+        _check(lib().gkl_grad(self._h, None if sb is None else sb.ctypes.data_as(ctypes.c_void_p), _ptr(Sb),
+                              _ptr(gw), _ptr(gs), min_relgap), self._h)
+        return gs, gw
+
+
+class GKLFunction(torch.autograd.Function):
+    """(s, w) -> (sigma, scores) with the gradient computed by gkl_grad.
+
+    forward: sets the per-sample weights s (n) and per-SNP weights w (m) on
+    the handle and runs the top-k solve; returns sigma (k, float64) and the PC
+    scores U diag(sigma) (n x k).  backward: dL/ds and dL/dw from the adjoints
+    of sigma and of the scores."""
+
+    @staticmethod
+    def forward(ctx, s, w, handle: GKL, solve_kw: dict, min_relgap: float):
+        handle.set_weights(s.detach(), w.detach())
+        r = handle.svd(**solve_kw)
+        if not r.converged:
+            raise GKLError(NOT_CONVERGED, "forward solve did not converge")
+        ctx.handle, ctx.min_relgap = handle, min_relgap
+        ctx.dtype = r.U.dtype
+        ctx.sdtype, ctx.wdtype = s.dtype, w.dtype
+        sigma = torch.tensor(r.sigma, dtype=torch.float64, device=r.U.device)
+        scores = r.U * sigma.to(r.U.dtype)[None, :]
+        return sigma, scores
+
+    @staticmethod
+    def backward(ctx, sigma_bar, scores_bar):
+        sb = None if sigma_bar is None else sigma_bar.detach().double().cpu().numpy()
+        gs, gw = ctx.handle.grad(sb, scores_bar, min_relgap=ctx.min_relgap, dtype=ctx.dtype)
+        return gs.to(ctx.sdtype), gw.to(ctx.wdtype), None, None, None

@@ -1,0 +1,91 @@
+"""Block form (GKL_BLOCK: blocks of b vectors, FP32 bases, FP64 projected
+matrix) against the FP64 oracle.
+
+Bars (FP32 bases and products): singular values 1e-5 relative to sigma_1,
+vector angles within 10 (residual + 3e-6 sigma_1) / gap, and the true residual
+||A^T u_i - sigma_i v_i|| (oracle products) within twice the reported block
+residual plus 1e-4 sigma_1 (FP32 rounding of the bases)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.helpers import oracle_matrix, small_geno, to_dev
+from tests.test_gpu_svd import angles, gaps
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gk():
+    import torch  # noqa: F401
+    from paper_1808_03374_gb300 import build, gkl
+    build()
+    return gkl
+
+
+def check(M, ref, r, k):
+    assert r.converged, r.info
+    assert np.all(np.diff(r.sigma) <= 0)
+    rel = np.abs(r.sigma - ref.sigma[:k]) / ref.sigma[0]
+    assert rel.max() < 1e-5, (rel.max(), r.sigma[:4], ref.sigma[:4])
+    U = r.U.double().cpu().numpy()
+    V = r.V.double().cpu().numpy()
+    g = gaps(ref.sigma)[:k]
+    bound = 10 * (np.maximum(r.resid, 0) + 3e-6 * ref.sigma[0]) / g + 1e-12
+    assert np.all(angles(V, ref.V[:, :k]) <= bound)
+    assert np.all(angles(U, ref.U[:, :k]) <= bound)
+    idx = np.argmax(np.abs(V), axis=0)
+    assert np.all(V[idx, np.arange(k)] > 0)
+    for i in range(k):
+        t = np.linalg.norm(M.rmatvec(U[:, i]) - r.sigma[i] * V[:, i])
+        assert t <= 2 * r.resid[i] + 1e-4 * ref.sigma[0]
+
+
+@pytest.mark.parametrize("b,ell", [(8, 48), (32, 128)])
+def test_block_admixture(gk, b, ell):
+    g = small_geno(1503, 9_001, pops=5, miss=0.02, seed=61)
+    M = oracle_matrix(g)
+    k = 10
+    ref = oracle.gkl(M, k=k + 2, ell=40, tol=1e-13, v0=synth.normal_vec(4, 0, g.m), maxit=2000)
+    assert ref.converged
+    h = gk.GKL(to_dev(g.packed), g.n)
+    r = h.svd(k=k, ell=ell, precision="block", block=b, tol=1e-6, maxit=200, seed=9)
+    check(M, ref, r, k)
+    assert r.info["matvec_pairs"] % b == 0
+
+
+def test_block_ragged_sizes(gk):
+    g = small_geno(301, 2_003, pops=3, miss=0.05, seed=62)
+    M = oracle_matrix(g)
+    ref = oracle.gkl(M, k=7, ell=30, tol=1e-13, v0=synth.normal_vec(5, 0, g.m), maxit=2000)
+    h = gk.GKL(to_dev(g.packed), g.n)
+    r = h.svd(k=5, ell=60, precision="block", block=12, tol=1e-6, maxit=200, seed=3)
+    check(M, ref, r, 5)
+
+
+def test_block_rank_deficient_replaces_directions(gk):
+    """Duplicated samples make A rank-deficient (rank <= 40): the block Krylov
+    space exhausts the range and the dependent directions are replaced by random
+    vectors; the top singular values are still found."""
+    from tests.test_oracle_core import pack_codes
+    n0, m = 40, 400
+    g = synth.genotypes(synth.GenoSpec(n=n0, m=m, n_pops=2, miss_rate=0.0, seed=29))
+    codes = np.stack([(g.packed >> (2 * t)) & 3 for t in range(4)], -1).reshape(m, -1)[:, :n0]
+    packed = pack_codes(np.concatenate([codes, codes[:, :24]], axis=1))
+    M = oracle.Matrix.from_packed(packed, 64)
+    sd = np.linalg.svd(M.dense(), compute_uv=False)
+    h = gk.GKL(to_dev(packed), 64)
+    r = h.svd(k=6, ell=48, precision="block", block=8, tol=1e-6, maxit=100, seed=4)
+    assert r.converged and r.info["breakdowns"] > 0
+    assert np.allclose(r.sigma, sd[:6], rtol=1e-5)
+
+
+def test_block_argument_errors(gk):
+    g = small_geno(200, 500, seed=63)
+    h = gk.GKL(to_dev(g.packed), g.n)
+    for kw in (dict(k=5, ell=40, block=33), dict(k=5, ell=40, block=24), dict(k=40, ell=40, block=8),
+               dict(k=5, ell=40, block=8, k_keep=7)):
+        with pytest.raises(gk.GKLError) as e:
+            h.svd(precision="block", tol=1e-6, **kw)
+        assert e.value.code == gk.ERR_ARG
