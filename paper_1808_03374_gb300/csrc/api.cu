@@ -564,13 +564,13 @@ int gkl_init(gkl_handle** out, const uint8_t* packed, int64_t n, int64_t m, int6
         gkl_destroy(h);
         return GKL_ERR_CUDA;
     }
-    // FP32 A^T u: GKL_RMV_KERNEL=tc selects the tcgen05 kernel, otherwise the
-    // mma.sync kernel runs
+    // FP32 A^T u runs on the tcgen05 kernel; GKL_RMV_KERNEL=mma selects the
+    // mma.sync kernel instead (kept for comparison)
     const char* rk = std::getenv("GKL_RMV_KERNEL");
-    if (rk && std::strcmp(rk, "tc") == 0)
-        tc_prepare(h);
-    else
+    if (rk && std::strcmp(rk, "mma") == 0)
         h->tc_state = -1;
+    else
+        tc_prepare(h);
     if (mu) {
         e = cudaMemcpyAsync(h->mu, mu, sizeof(double) * m, cudaMemcpyDefault, h->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->d, scale, sizeof(double) * m, cudaMemcpyDefault, h->stream);
@@ -661,6 +661,8 @@ int gkl_destroy(gkl_handle* h) {
     if (h->ws) cudaFree(h->ws);
     if (h->host_out) cudaFreeHost(h->host_out);
     if (h->aux) cudaFree(h->aux);
+    if (h->miss_off) cudaFree(h->miss_off);
+    if (h->miss_idx) cudaFree(h->miss_idx);
     if (h->last_U) cudaFree(h->last_U);
     if (h->gws) cudaFree(h->gws);
     delete h;

@@ -286,8 +286,32 @@ static cudaError_t download(BlockCtx& c, const double* src, std::vector<double>&
 
 // Orthonormalise X (len x q) against B (len x nb); returns R (q x q, column-major)
 // with X_before = X_after R (up to the replaced directions, whose rows of R are 0).
+static cudaError_t orthonormalize_once(BlockCtx& c, float* X, int64_t ldx, int q, const float* B, int64_t ldb,
+                                       int nb, int64_t len, std::vector<double>& R, bool& chol_ok);
+
+// The eigen step, replacement and Cholesky pass below are repeated (at most
+// three times) while the Cholesky pass meets a matrix that is not positive
+// definite in FP64 -- possible when replaced and kept directions are nearly
+// dependent after the FP32 products; each repetition starts from the block the
+// previous one produced, and the factors multiply.
 static cudaError_t orthonormalize(BlockCtx& c, float* X, int64_t ldx, int q, const float* B, int64_t ldb, int nb,
                                   int64_t len, std::vector<double>& R) {
+    R.assign((size_t)q * q, 0.0);
+    for (int i = 0; i < q; ++i) R[i + (size_t)q * i] = 1.0;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        std::vector<double> Ri;
+        bool ok = false;
+        cudaError_t e = orthonormalize_once(c, X, ldx, q, B, ldb, nb, len, Ri, ok);
+        if (e != cudaSuccess) return e;
+        R = matmul(q, Ri, R);
+        if (ok) return cudaSuccess;
+    }
+    return cudaErrorInvalidValue;
+}
+
+static cudaError_t orthonormalize_once(BlockCtx& c, float* X, int64_t ldx, int q, const float* B, int64_t ldb,
+                                       int nb, int64_t len, std::vector<double>& R, bool& chol_ok) {
+    chol_ok = false;
     cudaError_t e = cgs2(c, X, ldx, q, B, ldb, nb, len);
     std::vector<double> G, lam, Z;
     if (e == cudaSuccess) e = gram(c, X, ldx, q, X, ldx, q, len, c.d_small);
@@ -329,12 +353,16 @@ static cudaError_t orthonormalize(BlockCtx& c, float* X, int64_t ldx, int q, con
     if ((e = gram(c, X, ldx, q, X, ldx, q, len, c.d_small)) != cudaSuccess) return e;
     if ((e = download(c, c.d_small, G, (size_t)q * q)) != cudaSuccess) return e;
     std::vector<double> R2;
-    if (!cholesky(q, G, R2)) return cudaErrorInvalidValue;
+    if (!cholesky(q, G, R2)) {  // leave X as the eigen step made it; the caller repeats
+        R = R1;
+        return cudaGetLastError();
+    }
     const std::vector<double> R2i = inv_upper(q, R2);
     if ((e = upload(c, R2i, c.d_small)) != cudaSuccess) return e;
     k_block_axpy<<<axpy_grid(c, len), 256, 0, c.st>>>(X, ldx, q, X, ldx, q, c.d_small, 0.f, 1.f, len);
     c.launches += 1;
     R = matmul(q, R2, R1);
+    chol_ok = true;
     return cudaGetLastError();
 }
 

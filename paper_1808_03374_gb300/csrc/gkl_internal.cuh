@@ -100,6 +100,9 @@ struct gkl_handle {
     // tensor-core (tcgen05) A^T u: 0 = not prepared, 1 = ready, -1 = unavailable or disabled
     int tc_state;
     alignas(64) unsigned char tc_map[128];  // TMA descriptor of the packed matrix
+    int64_t* miss_off;   // CSR of the missing codes per SNP (m + 1 offsets), built by tc_prepare
+    uint32_t* miss_idx;  // sample indices, ascending per SNP
+    int64_t miss_nnz;
     char err[512];
 };
 
@@ -151,7 +154,7 @@ __global__ void __launch_bounds__(256) k_u_scale(const float* u, const float* s,
 __global__ void __launch_bounds__(256) k_rmv_mma_fin(const double* p1, const double* p3, int nb, int64_t m,
                                                       const double* mu, const double* d, const float* w,
                                                       const double* dsc, float* x, FinArgs fa, Sv sv);
-// tcgen05 A^T u (FP32 path, packed_tc.cu); tc_prepare builds the TMA descriptor once per handle.
+// tcgen05 A^T u (FP32 path, packed_tc.cu); tc_prepare builds the missing-code list once per handle.
 bool tc_prepare(gkl_handle* h);
 size_t rmv_tc_scratch_bytes(const gkl_handle* h);
 cudaError_t launch_rmatvec_tc(const gkl_handle* h, const float* u, float* x, void* scratch, const Sv* sv,

@@ -5,23 +5,39 @@
 //
 // The contraction over samples is exact integer arithmetic on the 5th-generation
 // tensor cores (tcgen05, kind::f8f6f4):
-//  * u~ in fixed point: u~'_i = S sum_{p<7} delta_{p,i} 16^-(p+1), S = 2^e >= max|u~|,
-//    digits delta in [-16, 16] (exact in e4m3), |u~ - u~'| <= 2^-29 S;
+//  * u~ in fixed point: u~'_i = S sum_{p<7} delta_{p,i} 16^-(p+1) = S z_i 2^-28,
+//    S = 2^e >= max|u~|, digits delta in [-16, 16] (exact in e4m3), z_i an
+//    integer, |u~ - u~'| <= 2^-29 S;
 //  * operand A (128 SNP rows x samples) is built in registers from the packed
-//    codes and written to tensor memory: H(c) = 1 + c/8 (e4m3 bits 0x38 | c, one
-//    LOP3 per four codes) and M(c) = 2^-6 [c == 3] (e4m3 bits 0x08);
+//    codes and written to tensor memory.  Code t (bits 2t, 2t+1) of a byte is
+//    read in place as e4m3: for t = 0, 2 (after one shift by 4 for t = 2) the
+//    code sits in mantissa bits 0-1, H_a(c) = 1 + c/8 (bits 0x38 | c); for
+//    t = 1, 3 it sits in bits 2-3 (mantissa MSB and exponent LSB), H_b(c) = 0.5,
+//    0.75, 1.0, 1.5 for c = 0..3 -- affine, 0.5 + c/4, on the observed codes.
+//    Five operations per 32-bit word of 16 codes;
 //  * operand B = the digit matrix (K samples x N = 16 columns, 7 used) in shared
-//    memory, 128-byte swizzled, K-major;
-//  * D_H[p] = sum_i (1 + c_i/8) delta_{p,i} and D_M[p] = 2^-6 sum_{i missing} delta_{p,i}
-//    accumulate in FP32 in tensor memory, exactly: every term is a multiple of
-//    2^-6 and a K-range of at most 64,000 samples keeps |D| * 64 below 2^24;
-//  * sum_{i obs} g_i delta_{p,i} = 8 (D_H[p] - sum_i delta_{p,i}) - 192 D_M[p] and
-//    sum_{i missing} delta_{p,i} = 64 D_M[p].
-// The packed tiles (128 rows x 64 bytes = 256 samples) arrive by TMA into a
-// shared-memory ring; the digit tiles by bulk copy.  Warp roles per CTA: one TMA
-// producer, one MMA issuer, eight decode warps (two per TMEM sub-partition, one
-// per half of the 256-sample stage) and four epilogue warps.  One persistent CTA
-// per SM walks work items (128-row tile, K-range).
+//    memory, 128-byte swizzled, K-major, the samples in the order the decode
+//    produces (class a: t = 0, 2 first, then class b: t = 1, 3);
+//  * eight FP32 accumulators in tensor memory (two classes x four K-step
+//    residues, so that consecutive MMAs never wait on one another), each exact:
+//    multiples of 1/8 below 2^21 for K-ranges of at most 64,000 samples;
+//  * the missing codes are sparse and fixed per matrix: their sample indices are
+//    listed once per SNP (CSR, built at the first use) and a gather kernel adds
+//    the z_i of the listed samples, as exact 64-bit integers per class, to
+//    Z_a and Z_b;
+//  * with S_a, S_b the digit sums of the two classes,
+//    sum_{obs} g u~' = S sum_p 16^-(p+1) (8 D_a[p] + 4 D_b[p]) - S sum_p 16^-(p+1) (8 S_a + 2 S_b)
+//                      - S 2^-28 (3 Z_a + 4 Z_b),
+//    sum_{missing} u~' = S 2^-28 (Z_a + Z_b).
+// Data movement: per 512-sample stage one TMA box of 128 rows x 128 bytes
+// (128-byte swizzle) brings the packed codes and one bulk copy the 8 KB digit
+// tile into a shared-memory ring.  (The copy engine walks a box row by row; a
+// 64-byte box width was measured at about 3 TB/s on this matrix.)  Warp roles
+// per CTA: one copy producer, one MMA issuer, sixteen decode warps (four per
+// TMEM sub-partition, one per 32-byte quarter of the stage) and four epilogue
+// warps.  One persistent CTA per SM walks work items (128-row tile, K-range),
+// the K-ranges of a tile consecutively so that each row is read as one
+// contiguous run (a range-major order measured 40% slower: DRAM locality).
 //
 // Every wait is bounded (about two seconds of clock); a wait that runs out sets
 // an error word that the host reads after the solve, and the kernel drains its
@@ -32,6 +48,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "epilogue.cuh"
 #include "gkl_internal.cuh"
@@ -40,20 +57,21 @@ namespace gkl {
 
 namespace {
 constexpr int kRows = 128;                 // SNP rows per tile = TMEM lanes = MMA M
-constexpr int kStageSamples = 256;         // samples per pipeline stage
-constexpr int kStageRowBytes = 64;         // packed bytes per row per stage
-constexpr int kStages = 10;                // shared-memory ring depth
-constexpr int kAbuf = 3;                   // tensor-memory operand buffers
-constexpr int kPackedBytes = kRows * kStageRowBytes;  // 8 KB per stage
-constexpr int kDigitBytes = 16 * kStageSamples;       // 4 KB per stage: 16 digit rows x 256 samples
+constexpr int kStageSamples = 512;         // samples per pipeline stage
+constexpr int kStageRowBytes = 128;        // packed bytes per row per stage
+constexpr int kStages = 8;                 // shared-memory ring depth
+constexpr int kPackedBytes = kRows * kStageRowBytes;  // 16 KB per stage
+constexpr int kDigitBytes = 16 * kStageSamples;       // 8 KB: 16 digit rows x 512 samples (4 swizzle atoms)
+constexpr int kAbuf = 2;                   // tensor-memory operand buffers (128 columns each)
 constexpr int kDigits = 7;
-constexpr int kMaxRangeStages = 250;       // 64,000 samples per K-range
-constexpr int kThreads = 448;              // 14 warps
-constexpr int kDecodeWarp0 = 2, kEpiWarp0 = 10;
+constexpr int kMaxRangeStages = 125;       // 64,000 samples per K-range
+constexpr int kThreads = 704;              // 22 warps
+constexpr int kDecodeWarps = 16;
+constexpr int kDecodeWarp0 = 2, kEpiWarp0 = kDecodeWarp0 + kDecodeWarps;
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kColD = 384;            // accumulators: 2 x (16 H + 16 M) columns
+constexpr uint32_t kColD = 256;            // accumulators: 2 sets x 8 x 16 columns
 constexpr int kBarOff = kStages * (kPackedBytes + kDigitBytes);
-constexpr int kSmemBytes = 1024 + kBarOff + 512;
+constexpr int kSmemBytes = 1024 + kBarOff + 1024;
 // instruction descriptor: FP32 accumulate (bits 4-5 = 1), A = B = e4m3 (0), K-major
 // A and B, N = 16 (bits 17-22: N >> 3), M = 128 (bits 24-28: M >> 4)
 constexpr uint32_t kIdesc = (1u << 4) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
@@ -73,19 +91,22 @@ __device__ __forceinline__ void bar_arrive(uint32_t a) {
 __device__ __forceinline__ void bar_expect_tx(uint32_t a, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(a), "r"(bytes) : "memory");
 }
-// Bounded wait for the phase of parity `par` to complete.
+__device__ __forceinline__ bool bar_test(uint32_t a, uint32_t par) {
+    uint32_t ok;
+    asm volatile("{.reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p;}\n"
+                 : "=r"(ok)
+                 : "r"(a), "r"(par)
+                 : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase of parity `par` to complete (the clock is read
+// only once the first test has failed).
 __device__ __forceinline__ bool bar_wait(uint32_t a, uint32_t par) {
+    if (bar_test(a, par)) return true;
     const long long t0 = clock64();
-    while (true) {
-        uint32_t ok;
-        asm volatile(
-            "{.reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p;}\n"
-            : "=r"(ok)
-            : "r"(a), "r"(par)
-            : "memory");
-        if (ok) return true;
+    while (!bar_test(a, par))
         if (clock64() - t0 > kWaitCycles) return false;
-    }
+    return true;
 }
 __device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
     asm volatile(
@@ -114,14 +135,12 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
     asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
-        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n" ::"r"(taddr),
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(
+            taddr),
         "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
-        "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
-        "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
         : "memory");
 }
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
@@ -139,25 +158,31 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 
 // ---- digits of u~ -----------------------------------------------------------
 
-// Position of sample `loc` (0..255) of a stage along the MMA's K axis.  The
-// decode turns a 32-bit code word (16 samples; code t of byte b is sample 4b+t)
-// into four operand words H_t holding samples t, 4+t, 8+t, 12+t, so K index
-// 16w + 4t + b carries sample 16w + 4b + t: a 4x4 transpose inside every
-// aligned group of 16 samples.
-__host__ __device__ inline int tc_k_of_sample(int loc) { return (loc & ~15) | ((loc & 3) << 2) | ((loc >> 2) & 3); }
+// Position of sample `loc` (0..511) of a stage along the MMA's K axis.  Decode
+// warp q (0..3) reads bytes 32q..32q+31 of each row: code words w = 0..7 of 16
+// samples (sample 128q + 16w + 4b + t is code t of byte b).  Its operand words
+// go to tensor-memory column 16q + 2w + (t >> 1) of the class-(t & 1) region
+// (64 columns = 256 K bytes each), byte b of the column being K index
+// 4 * column + b.
+__host__ __device__ inline int tc_k_of_sample(int loc) {
+    const int q = loc >> 7, w = (loc >> 4) & 7, b = (loc >> 2) & 3, t = loc & 3;
+    return (t & 1) * 256 + 4 * (16 * q + 2 * w + (t >> 1)) + b;
+}
 
-// Byte offset of (digit row p, K index kk) inside a stage's 4 KB digit tile:
-// two 128-byte-swizzled atoms of 16 rows x 128 K each.
+// Byte offset of (digit row p, K index kk) inside a stage's 8 KB digit tile:
+// four 128-byte-swizzled atoms of 16 rows x 128 K each.
 __host__ __device__ inline int tc_digit_offset(int p, int kk) {
     const int atom = kk >> 7, b = kk & 127;
     return atom * 2048 + p * 128 + ((((b >> 4) ^ (p & 7))) << 4) + (b & 15);
 }
 
-// One block per stage (256 samples): digits in e4m3 into the stage's tile and
-// the stage's digit sums (exact integers) into cs[stage][p].
-__global__ void __launch_bounds__(256) k_u_digits_tc(const float* __restrict__ u, const float* __restrict__ s,
+// One block per stage (512 samples): digits in e4m3 into the stage's tile, z_i
+// (int32) into z[], and the stage's digit sums per operand class (exact
+// integers) into cs[stage][16]: [class a: p = 0..6 | class b: 8 + p].
+__global__ void __launch_bounds__(512) k_u_digits_tc(const float* __restrict__ u, const float* __restrict__ s,
                                                       int64_t n, const double* __restrict__ dsc,
-                                                      uint8_t* __restrict__ dig, int* __restrict__ cs) {
+                                                      uint8_t* __restrict__ dig, int* __restrict__ cs,
+                                                      int* __restrict__ zout) {
     const int st = blockIdx.x, loc = threadIdx.x;
     const int64_t i = (int64_t)st * kStageSamples + loc;
     double x = 0.0;
@@ -165,6 +190,7 @@ __global__ void __launch_bounds__(256) k_u_digits_tc(const float* __restrict__ u
     uint8_t* tile = dig + (size_t)st * kDigitBytes;
     const int kk = tc_k_of_sample(loc);
     int sums[kDigits];
+    int z = 0;
 #pragma unroll
     for (int p = 0; p < 16; ++p) {
         int dg = 0;
@@ -174,51 +200,41 @@ __global__ void __launch_bounds__(256) k_u_digits_tc(const float* __restrict__ u
             x -= rd;
             dg = (int)rd;
             sums[p] = dg;
+            z = 16 * z + dg;
         }
         tile[tc_digit_offset(p, kk)] = (uint8_t)__nv_cvt_float_to_fp8((float)dg, __NV_SATFINITE, __NV_E4M3);
     }
-    __shared__ int red[8][kDigits];
+    zout[i] = z;
+    // lanes of one warp alternate classes (t = loc & 3): reduce even and odd lanes separately
+    __shared__ int red[16][2][kDigits];
+    const int cls = loc & 1;
 #pragma unroll
     for (int p = 0; p < kDigits; ++p) {
         int v = sums[p];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((loc & 31) == 0) red[loc >> 5][p] = v;
+        for (int o = 16; o > 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((loc & 31) < 2) red[loc >> 5][cls][p] = v;
     }
     __syncthreads();
-    if (loc < kDigits) {
+    if (loc < 2 * kDigits) {
+        const int c = loc / kDigits, p = loc % kDigits;
         int t = 0;
-        for (int w = 0; w < 8; ++w) t += red[w][loc];
-        cs[(size_t)st * 8 + loc] = t;
+        for (int w = 0; w < 16; ++w) t += red[w][c][p];
+        cs[(size_t)st * 16 + 8 * c + p] = t;
     }
 }
 
 // ---- main kernel ------------------------------------------------------------
 
 struct TcArgs {
-    const uint8_t* dig;  // nstages x 4 KB digit tiles
-    const int* cs;       // nstages x 8 digit sums
+    const uint8_t* dig;  // nstages x 8 KB digit tiles
+    const int* cs;       // nstages x 16 digit sums per class
     int nstages, range_stages, nranges, ntiles;
     int64_t m;
     const double* dsc;   // {S, 1/S, sum u~}
-    double* p1;          // nranges x m: S sum_p 16^-(p+1) sum_{i obs} g_i delta_{p,i} (range 0 carries the offset)
-    double* p3;          // nranges x m: S sum_p 16^-(p+1) sum_{i missing} delta_{p,i} (+ correction in range 0)
+    double* p1;          // nranges x m: S sum_p 16^-(p+1) (8 D_a + 4 D_b) over the range (range 0: - offsets)
+    double* p3;          // nranges x m: 0 (range 0: sum u~ - sum u~'); the missing terms are added later
     int* err;            // set to a nonzero code if a wait ran out
 };
-
-// Operand words of one 32-bit code word W (16 samples): H_t = 0x38 | code_t and
-// M_t = 0x08 [code_t == 3] in each byte, for code positions t = 0..3.
-__device__ __forceinline__ void decode_word(uint32_t W, uint32_t* H, uint32_t* M) {
-    const uint32_t w2 = W >> 2, w4 = W >> 4, w6 = W >> 6;
-    H[0] = (W & 0x03030303u) | 0x38383838u;
-    H[1] = (w2 & 0x03030303u) | 0x38383838u;
-    H[2] = (w4 & 0x03030303u) | 0x38383838u;
-    H[3] = (w6 & 0x03030303u) | 0x38383838u;
-    // [code_t == 3] = bit 2t & bit 2t+1 of each byte, moved to bit 3
-    M[0] = (W << 3) & (W << 2) & 0x08080808u;
-    M[1] = (W << 1) & W & 0x08080808u;
-    M[2] = (W >> 1) & w2 & 0x08080808u;
-    M[3] = (W >> 3) & w4 & 0x08080808u;
-}
 
 __global__ void __launch_bounds__(kThreads, 1) k_rmv_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
     extern __shared__ uint8_t smem_raw[];
@@ -232,9 +248,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_rmv_tc(const __grid_constant__ 
     auto aempty = [&](int t) { return sBar + 8u * (2 * kStages + kAbuf + t); };
     auto dfull = [&](int q) { return sBar + 8u * (2 * kStages + 2 * kAbuf + q); };
     auto dempty = [&](int q) { return sBar + 8u * (2 * kStages + 2 * kAbuf + 2 + q); };
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sbase + kBarOff + 256);
-    int* s_fail = reinterpret_cast<int*>(sbase + kBarOff + 260);
-    double* s_csum = reinterpret_cast<double*>(sbase + kBarOff + 264);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sbase + kBarOff + 384);
+    double* s_csum = reinterpret_cast<double*>(sbase + kBarOff + 392);     // [2]
+    long long* s_c = reinterpret_cast<long long*>(sbase + kBarOff + 512);  // [4 warps][2][kDigits]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0) {
@@ -248,14 +264,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_rmv_tc(const __grid_constant__ 
             bar_init(empty(s), 1);
         }
         for (int t = 0; t < kAbuf; ++t) {
-            bar_init(afull(t), 8);
+            bar_init(afull(t), kDecodeWarps);
             bar_init(aempty(t), 1);
         }
         for (int q = 0; q < 2; ++q) {
             bar_init(dfull(q), 1);
             bar_init(dempty(q), 4);
         }
-        *s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     tc_fence_before();
@@ -263,18 +278,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_rmv_tc(const __grid_constant__ 
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const int nitems = a.ntiles * a.nranges;
-    auto fail = [&](int code) {
-        *s_fail = 1;
-        atomicCAS(a.err, 0, code);
-    };
+    auto fail = [&](int code) { atomicCAS(a.err, 0, code); };
 
     if (warp == 0) {
-        // ---- TMA producer
+        // ---- copy producer: per stage one TMA box (packed) + one bulk copy (digits)
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-                const int tile = item % a.ntiles, range = item / a.ntiles;
+                const int tile = item / a.nranges, range = item % a.nranges;
                 const int st0 = range * a.range_stages, nst = min(a.range_stages, a.nstages - st0);
                 for (int k = 0; k < nst; ++k, ++it) {
                     const int s = (int)(it % kStages);
@@ -294,12 +306,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_rmv_tc(const __grid_constant__ 
                 if (!bar_wait(full((int)(q % kStages)), (q / kStages) & 1u)) fail(2);
         }
     } else if (warp == 1) {
-        // ---- MMA issuer
+        // ---- MMA issuer: per stage 16 MMAs (class a, b x eight 32-byte K-steps) into 8 accumulators.
+        // The decode warps arrive on afull only after they have seen the stage's copies land.
         if (lane == 0) {
             uint32_t it = 0, li = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
-                const int range = item / a.ntiles;
+                const int range = item % a.nranges;
                 const int st0 = range * a.range_stages, nst = min(a.range_stages, a.nstages - st0);
                 const uint32_t acc = li & 1u;
                 if (!bar_wait(dempty(acc), ((li >> 1) & 1u) ^ 1u)) {
@@ -307,23 +320,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_rmv_tc(const __grid_constant__ 
                     break;
                 }
                 tc_fence_after();
-                const uint32_t dH = tmem + kColD + 32u * acc, dM = dH + 16u;
+                const uint32_t dbase = tmem + kColD + 128u * acc;
                 for (int k = 0; k < nst; ++k, ++it) {
                     const int s = (int)(it % kStages), t = (int)(it % kAbuf);
-                    if (!bar_wait(afull(t), (it / kAbuf) & 1u) || !bar_wait(full(s), (it / kStages) & 1u)) {
+                    if (!bar_wait(afull(t), (it / kAbuf) & 1u)) {
                         fail(4);
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t aH = tmem + 128u * t, aM = aH + 64u;
-                    const uint32_t bs = sDig + s * kDigitBytes;
+                    const uint32_t aA = tmem + 128u * t;
+                    const uint64_t d0 = desc_sw128(sDig + s * kDigitBytes);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        mma_e4m3_ts(dH, aH + 8u * q, desc_sw128(bs + (q >> 2) * 2048 + 32 * (q & 3)), (k | q) != 0);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        mma_e4m3_ts(dM, aM + 8u * q, desc_sw128(bs + (q >> 2) * 2048 + 32 * (q & 3)), (k | q) != 0);
+                    for (int i = 0; i < 8; ++i) {
+                        // K-step i: 32 bytes = 8 columns; descriptor address in 16-byte units
+                        // (+2 per 32 bytes, +128 per 2 KB atom); atoms 0-1 class a, 2-3 class b
+                        const uint32_t acc_in = (k != 0) || (i >= 4);
+                        const uint64_t dd = d0 + (uint64_t)(128 * (i >> 2) + 2 * (i & 3));
+                        mma_e4m3_ts(dbase + 16u * (i & 3), aA + 8u * i, dd, acc_in);
+                        mma_e4m3_ts(dbase + 64u + 16u * (i & 3), aA + 64u + 8u * i, dd + 256, acc_in);
+                    }
                     mma_commit(aempty(t));
                     mma_commit(empty(s));
                 }
@@ -336,34 +352,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_rmv_tc(const __grid_constant__ 
             }
         }
     } else if (warp < kEpiWarp0) {
-        // ---- decode: row = lane of this warp's TMEM sub-partition, half of the stage
-        const int sub = warp & 3, half = (warp - kDecodeWarp0) >> 2;
+        // ---- decode: row = lane of this warp's TMEM sub-partition, 32-byte quarter q of the stage
+        const int sub = warp & 3, q = (warp - kDecodeWarp0) >> 2;
         const int row = 32 * sub + lane;
         const uint32_t lane_base = (uint32_t)(32 * sub) << 16;
         uint32_t it = 0;
         bool ok = true;
         for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-            const int range = item / a.ntiles;
+            const int range = item % a.nranges;
             const int st0 = range * a.range_stages, nst = min(a.range_stages, a.nstages - st0);
             for (int k = 0; k < nst; ++k, ++it) {
                 const int s = (int)(it % kStages), t = (int)(it % kAbuf);
-                if (!bar_wait(full(s), (it / kStages) & 1u) || !bar_wait(aempty(t), ((it / kAbuf) & 1u) ^ 1u)) {
+                if (!bar_wait(full(s), (it / kStages) & 1u)) {
                     fail(6);
                     ok = false;
                     break;
                 }
-                // 64-byte swizzle of the TMA tile: chunk c of row r sits at chunk c ^ ((r >> 1) & 3)
+                // 128-byte swizzle of the TMA tile: 16-byte chunk c of row r sits at chunk c ^ (r & 7)
                 const uint8_t* rp = sbase + s * kPackedBytes + row * kStageRowBytes;
-                const int sw = (row >> 1) & 3;
-                const uint4 q0 = *reinterpret_cast<const uint4*>(rp + (((2 * half) ^ sw) << 4));
-                const uint4 q1 = *reinterpret_cast<const uint4*>(rp + (((2 * half + 1) ^ sw) << 4));
+                const uint4 q0 = *reinterpret_cast<const uint4*>(rp + (((2 * q) ^ (row & 7)) << 4));
+                const uint4 q1 = *reinterpret_cast<const uint4*>(rp + (((2 * q + 1) ^ (row & 7)) << 4));
                 const uint32_t W[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-                uint32_t H[32], M[32];
+                uint32_t ha[16], hb[16];
 #pragma unroll
-                for (int w = 0; w < 8; ++w) decode_word(W[w], H + 4 * w, M + 4 * w);
-                const uint32_t col = tmem + lane_base + 128u * t + 32u * half;
-                tmem_st32(col, H);
-                tmem_st32(col + 64u, M);
+                for (int w = 0; w < 8; ++w) {
+                    const uint32_t Wv = W[w], W4 = Wv >> 4;
+                    ha[2 * w] = (Wv & 0x03030303u) | 0x38383838u;
+                    ha[2 * w + 1] = (W4 & 0x03030303u) | 0x38383838u;
+                    hb[2 * w] = (Wv & 0x0C0C0C0Cu) | 0x30303030u;
+                    hb[2 * w + 1] = (W4 & 0x0C0C0C0Cu) | 0x30303030u;
+                }
+                if (!bar_wait(aempty(t), ((it / kAbuf) & 1u) ^ 1u)) {
+                    fail(7);
+                    ok = false;
+                    break;
+                }
+                const uint32_t col = tmem + lane_base + 128u * t + 16u * q;
+                tmem_st16(col, ha);
+                tmem_st16(col + 64u, hb);
                 asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
                 tc_fence_before();
                 __syncwarp();
@@ -374,57 +400,74 @@ __global__ void __launch_bounds__(kThreads, 1) k_rmv_tc(const __grid_constant__ 
         // ---- epilogue
         const int sub = warp & 3, et = threadIdx.x - 32 * kEpiWarp0;
         const uint32_t lane_base = (uint32_t)(32 * sub) << 16;
-        // sum over all samples of u~' / S = sum_p 16^-(p+1) sum_i delta_{p,i}, exactly
-        long long* s_c = reinterpret_cast<long long*>(sbase + kBarOff + 272);  // [4][kDigits]
+        // class digit sums over all samples: s_csum[0] = sum_p 16^-(p+1) (S_a + S_b) = sum u~'/S,
+        // s_csum[1] = sum_p 16^-(p+1) (8 S_a + 2 S_b), the offsets of H_a and H_b, exactly
         {
-            long long c[kDigits] = {0, 0, 0, 0, 0, 0, 0};
+            long long c[2][kDigits];
+#pragma unroll
+            for (int p = 0; p < kDigits; ++p) c[0][p] = c[1][p] = 0;
             for (int st = et; st < a.nstages; st += 128)
 #pragma unroll
-                for (int p = 0; p < kDigits; ++p) c[p] += a.cs[(size_t)st * 8 + p];
+                for (int p = 0; p < kDigits; ++p) {
+                    c[0][p] += a.cs[(size_t)st * 16 + p];
+                    c[1][p] += a.cs[(size_t)st * 16 + 8 + p];
+                }
 #pragma unroll
-            for (int p = 0; p < kDigits; ++p) {
-                for (int o = 16; o > 0; o >>= 1) c[p] += __shfl_xor_sync(0xffffffffu, c[p], o);
-                if (lane == 0) s_c[(warp - kEpiWarp0) * kDigits + p] = c[p];
-            }
+            for (int cl = 0; cl < 2; ++cl)
+#pragma unroll
+                for (int p = 0; p < kDigits; ++p) {
+                    long long v = c[cl][p];
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0) s_c[((warp - kEpiWarp0) * 2 + cl) * kDigits + p] = v;
+                }
         }
         asm volatile("bar.sync 1, 128;\n" ::: "memory");
         if (et == 0) {
-            double t = 0.0;
+            double t0 = 0.0, t1 = 0.0;
             for (int p = kDigits - 1; p >= 0; --p) {
-                const long long c = s_c[p] + s_c[kDigits + p] + s_c[2 * kDigits + p] + s_c[3 * kDigits + p];
-                t += ldexp((double)c, -4 * (p + 1));
+                long long ca = 0, cb = 0;
+                for (int w = 0; w < 4; ++w) {
+                    ca += s_c[(w * 2 + 0) * kDigits + p];
+                    cb += s_c[(w * 2 + 1) * kDigits + p];
+                }
+                t0 += ldexp((double)(ca + cb), -4 * (p + 1));
+                t1 += ldexp((double)(8 * ca + 2 * cb), -4 * (p + 1));
             }
-            *s_csum = t;
+            s_csum[0] = t0;
+            s_csum[1] = t1;
         }
         asm volatile("bar.sync 1, 128;\n" ::: "memory");
-        const double S = a.dsc[0], usum = S * *s_csum;
+        const double S = a.dsc[0], usum = S * s_csum[0], hoff = S * s_csum[1];
         uint32_t li = 0;
         for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++li) {
-            const int tile = item % a.ntiles, range = item / a.ntiles;
+            const int tile = item / a.nranges, range = item % a.nranges;
             const uint32_t acc = li & 1u;
             if (!bar_wait(dfull(acc), (li >> 1) & 1u)) {
-                fail(7);
+                fail(8);
                 break;
             }
             tc_fence_after();
-            uint32_t r[32];
-            tmem_ld32(tmem + lane_base + kColD + 32u * acc, r);
+            const int64_t j = (int64_t)tile * kRows + 32 * sub + lane;
+            double hs = 0.0;
+            {
+                uint32_t r[32];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {  // accumulators 2h, 2h+1: class a (h < 2) or b
+                    tmem_ld32(tmem + lane_base + kColD + 128u * acc + 32u * h, r);
+                    const double wgt = h < 2 ? 8.0 : 4.0;
+#pragma unroll
+                    for (int p = kDigits - 1; p >= 0; --p)
+                        hs += ldexp(wgt, -4 * (p + 1)) *
+                              ((double)__uint_as_float(r[p]) + (double)__uint_as_float(r[16 + p]));
+                }
+            }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) bar_arrive(dempty(acc));
-            const int64_t j = (int64_t)tile * kRows + 32 * sub + lane;
             if (j < a.m) {
-                double hs = 0.0, ms = 0.0;
-#pragma unroll
-                for (int p = kDigits - 1; p >= 0; --p) {
-                    const double f = ldexp(1.0, -4 * (p + 1));
-                    const double dh = (double)__uint_as_float(r[p]), dm = (double)__uint_as_float(r[16 + p]);
-                    hs += f * (8.0 * dh - 192.0 * dm);
-                    ms += f * dm;
-                }
-                double P1 = S * hs, P3 = 64.0 * S * ms;
+                double P1 = S * hs, P3 = 0.0;
                 if (range == 0) {
-                    P1 -= 8.0 * usum;          // the offset 1 of H(c) over all samples
+                    P1 -= hoff;                // the offsets of H_a and H_b over all samples
                     P3 += a.dsc[2] - usum;     // so that sum u~ - sum_r p3 = sum_{obs} u~'
                 }
                 a.p1[(int64_t)range * a.m + j] = P1;
@@ -440,11 +483,96 @@ __global__ void __launch_bounds__(kThreads, 1) k_rmv_tc(const __grid_constant__ 
     }
 }
 
+// ---- missing-code list (CSR) and the per-product gather ----------------------
+
+// counts[j] = missing codes of SNP j among samples 0..n-1; one warp per SNP.
+__global__ void __launch_bounds__(256) k_miss_count(const uint8_t* __restrict__ packed, int64_t stride, int64_t n,
+                                                     int64_t m, int* __restrict__ counts) {
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= m) return;
+    const uint32_t* row = reinterpret_cast<const uint32_t*>(packed + j * stride);
+    const int64_t words = (n + 15) / 16;
+    int c = 0;
+    for (int64_t wd = lane; wd < words; wd += 32) {
+        uint32_t Y = row[wd] & (row[wd] >> 1) & 0x55555555u;
+        const int64_t valid = n - wd * 16;  // samples of this word below n
+        if (valid < 16) Y &= (1u << (2 * valid)) - 1u;
+        c += __popc(Y);
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) counts[j] = c;
+}
+
+// idx[off[j] ..] = the missing sample indices of SNP j, ascending; one warp per SNP.
+__global__ void __launch_bounds__(256) k_miss_fill(const uint8_t* __restrict__ packed, int64_t stride, int64_t n,
+                                                    int64_t m, const int64_t* __restrict__ off,
+                                                    uint32_t* __restrict__ idx) {
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= m) return;
+    const uint32_t* row = reinterpret_cast<const uint32_t*>(packed + j * stride);
+    const int64_t words = (n + 15) / 16;
+    int64_t pos = off[j];
+    for (int64_t w0 = 0; w0 < words; w0 += 32) {
+        const int64_t wd = w0 + lane;
+        uint32_t Y = 0;
+        if (wd < words) {
+            Y = row[wd] & (row[wd] >> 1) & 0x55555555u;
+            const int64_t valid = n - wd * 16;
+            if (valid < 16) Y &= (1u << (2 * valid)) - 1u;
+        }
+        const int c = __popc(Y);
+        int incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        int64_t p = pos + incl - c;
+        while (Y) {
+            const int bit = __ffs(Y) - 1;
+            Y &= Y - 1u;
+            idx[p++] = (uint32_t)(wd * 16 + (bit >> 1));
+        }
+        pos += __shfl_sync(0xffffffffu, incl, 31);
+    }
+}
+
+// Missing terms of A^T u for SNP j (one warp per SNP): Z_a, Z_b = sums of z_i over
+// the listed samples of class a (i even) and b (i odd), exact in 64-bit integers;
+// p1[j] -= S 2^-28 (3 Z_a + 4 Z_b), p3[j] += S 2^-28 (Z_a + Z_b) (range-0 partials).
+__global__ void __launch_bounds__(256) k_miss_gather(const int64_t* __restrict__ off, const uint32_t* __restrict__ idx,
+                                                      int64_t m, const int* __restrict__ z,
+                                                      const double* __restrict__ dsc, double* __restrict__ p1,
+                                                      double* __restrict__ p3) {
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= m) return;
+    long long za = 0, zb = 0;
+    for (int64_t e = off[j] + lane; e < off[j + 1]; e += 32) {
+        const uint32_t i = idx[e];
+        const long long v = z[i];
+        if (i & 1u)
+            zb += v;
+        else
+            za += v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        za += __shfl_xor_sync(0xffffffffu, za, o);
+        zb += __shfl_xor_sync(0xffffffffu, zb, o);
+    }
+    if (lane == 0 && (za | zb)) {
+        const double zs = ldexp(dsc[0], -28);
+        p1[j] -= zs * (double)(3 * za + 4 * zb);
+        p3[j] += zs * (double)(za + zb);
+    }
+}
+
 // ---- host side --------------------------------------------------------------
 
 struct TcPlan {
     int nstages, range_stages, nranges, ntiles, grid;
-    size_t dig_bytes, cs_bytes, part_bytes;
+    size_t dig_bytes, cs_bytes, z_bytes, part_bytes;
 };
 
 static TcPlan plan_tc(const gkl_handle* h) {
@@ -471,19 +599,23 @@ static TcPlan plan_tc(const gkl_handle* h) {
     p.nranges = (p.nstages + p.range_stages - 1) / p.range_stages;
     p.grid = (int)std::min<int64_t>((int64_t)p.ntiles * p.nranges, sms);
     p.dig_bytes = (size_t)p.nstages * kDigitBytes;
-    p.cs_bytes = (size_t)p.nstages * 8 * sizeof(int);
+    p.cs_bytes = (size_t)p.nstages * 16 * sizeof(int);
+    p.z_bytes = (size_t)p.nstages * kStageSamples * sizeof(int);
     p.part_bytes = 2 * (size_t)p.nranges * (size_t)h->m * sizeof(double);
     return p;
 }
 
 size_t rmv_tc_scratch_bytes(const gkl_handle* h) {
     const TcPlan p = plan_tc(h);
-    return p.dig_bytes + ((p.cs_bytes + 255) & ~(size_t)255) + p.part_bytes + 256;
+    return p.dig_bytes + ((p.cs_bytes + 255) & ~(size_t)255) + ((p.z_bytes + 255) & ~(size_t)255) + p.part_bytes +
+           256;
 }
 
-// Builds the TMA descriptor of the packed matrix (64-byte x 128-row boxes,
-// 64-byte swizzle).  Returns false if the driver entry point or the encoding is
-// unavailable or the buffer is not 16-byte aligned.
+// Prepares the tensor-core path for a handle: the TMA descriptor of the packed
+// matrix (128-byte x 128-row boxes, 128-byte swizzle), the kernel's shared-memory
+// limit and the list of missing codes per SNP.  Returns false (the mma.sync
+// kernel stays in use) if the driver entry point or a step is unavailable or
+// the packed buffer is not 16-byte aligned.
 bool tc_prepare(gkl_handle* h) {
     if (h->tc_state != 0) return h->tc_state > 0;
     h->tc_state = -1;
@@ -500,13 +632,38 @@ bool tc_prepare(gkl_handle* h) {
     const cuuint32_t box[2] = {(cuuint32_t)kStageRowBytes, (cuuint32_t)kRows};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(h->packed), gdim, gstride, box,
-                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return false;
     static_assert(sizeof(CUtensorMap) == sizeof(h->tc_map), "tensor map size");
     memcpy(h->tc_map, &map, sizeof(map));
     if (cudaFuncSetAttribute(k_rmv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess)
         return false;
+    // list of missing codes per SNP (CSR), built once: counts, host prefix sum, fill
+    const int64_t m = h->m;
+    int* counts = nullptr;
+    std::vector<int> hc((size_t)m);
+    std::vector<int64_t> ho((size_t)m + 1);
+    const unsigned wblocks = (unsigned)((m * 32 + 255) / 256);
+    cudaError_t e = cudaMalloc(&counts, sizeof(int) * m);
+    if (e == cudaSuccess) {
+        k_miss_count<<<wblocks, 256, 0, h->stream>>>(h->packed, h->stride, h->n, m, counts);
+        e = cudaMemcpyAsync(hc.data(), counts, sizeof(int) * m, cudaMemcpyDeviceToHost, h->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (counts) cudaFree(counts);
+    if (e != cudaSuccess) return false;
+    ho[0] = 0;
+    for (int64_t j = 0; j < m; ++j) ho[j + 1] = ho[j] + hc[j];
+    h->miss_nnz = ho[m];
+    e = cudaMalloc(&h->miss_off, sizeof(int64_t) * (m + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&h->miss_idx, sizeof(uint32_t) * std::max<int64_t>(1, h->miss_nnz));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->miss_off, ho.data(), sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        k_miss_fill<<<wblocks, 256, 0, h->stream>>>(h->packed, h->stride, h->n, m, h->miss_off, h->miss_idx);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return false;
     h->tc_state = 1;
     return true;
 }
@@ -516,7 +673,8 @@ cudaError_t launch_rmatvec_tc(const gkl_handle* h, const float* u, float* x, voi
     const TcPlan p = plan_tc(h);
     uint8_t* dig = static_cast<uint8_t*>(scratch);
     int* cs = reinterpret_cast<int*>(dig + p.dig_bytes);
-    double* p1 = reinterpret_cast<double*>(reinterpret_cast<char*>(cs) + ((p.cs_bytes + 255) & ~(size_t)255));
+    int* z = reinterpret_cast<int*>(reinterpret_cast<char*>(cs) + ((p.cs_bytes + 255) & ~(size_t)255));
+    double* p1 = reinterpret_cast<double*>(reinterpret_cast<char*>(z) + ((p.z_bytes + 255) & ~(size_t)255));
     double* p3 = p1 + (size_t)p.nranges * h->m;
     double* aux = h->aux;  // dsc[4] | counter | partials of the scale pass; error word at kAuxErrOffset
     double* dsc = aux;
@@ -526,20 +684,22 @@ cudaError_t launch_rmatvec_tc(const gkl_handle* h, const float* u, float* x, voi
     cudaStream_t st = h->stream;
     const int sblocks = std::min(2 * h->num_sms, (int)((h->n + 255) / 256));
     k_u_scale<<<std::max(1, sblocks), 256, 0, st>>>(u, h->s, h->n, part, counter, dsc);
-    k_u_digits_tc<<<p.nstages, 256, 0, st>>>(u, h->s, h->n, dsc, dig, cs);
+    k_u_digits_tc<<<p.nstages, kStageSamples, 0, st>>>(u, h->s, h->n, dsc, dig, cs, z);
     alignas(64) CUtensorMap map;
     memcpy(&map, h->tc_map, sizeof(map));
     TcArgs a{dig, cs, p.nstages, p.range_stages, p.nranges, p.ntiles, h->m, dsc, p1, p3, err};
     if (ev0) cudaEventRecord(ev0, st);
     k_rmv_tc<<<p.grid, kThreads, kSmemBytes, st>>>(map, a);
     if (ev1) cudaEventRecord(ev1, st);
+    k_miss_gather<<<(unsigned)((h->m * 32 + 255) / 256), 256, 0, st>>>(h->miss_off, h->miss_idx, h->m, z, dsc, p1,
+                                                                       p3);
     FinArgs f{};
     Sv s{};
     if (fa) f = *fa;
     if (sv) s = *sv;
     k_rmv_mma_fin<<<(unsigned)((h->m + 255) / 256), 256, 0, st>>>(p1, p3, p.nranges, h->m, h->mu, h->d, h->w, dsc, x,
                                                                     f, s);
-    if (nlaunch) *nlaunch = 4;
+    if (nlaunch) *nlaunch = 5;
     return cudaGetLastError();
 }
 
