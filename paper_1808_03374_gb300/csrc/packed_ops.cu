@@ -295,16 +295,18 @@ __device__ inline void finish_norm(const Sv& sv, int role, int j) {
     release_counter(&sv.sc->counter);
 }
 
-// Final reduction of A v over SNP chunks (fixed order), sample weights,
-// optional subtraction of earlier basis vectors, optional norm + step logic.
+// Final reduction of A v over SNP chunks, sample weights, optional
+// subtraction of earlier basis vectors, optional norm + step logic.  A block
+// takes 32 outputs at a time; its eight warps sum every eighth chunk (coalesced
+// over the outputs) and the eight partial sums are added in a fixed order.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_mv_fin(const T* __restrict__ part, int64_t ldp, int chunks, int64_t n,
-                                                     const float* __restrict__ s, T* __restrict__ y, FinArgs fa,
-                                                     Sv sv) {
+__global__ void __launch_bounds__(256) k_mv_fin(const T* __restrict__ part, int64_t ldp, int chunks, int64_t n,
+                                                const float* __restrict__ s, T* __restrict__ y, FinArgs fa, Sv sv) {
     if (fa.role != ROLE_NONE && sv.sc->abort) return;
     __shared__ double sb[GKL_MAX_ELL];
     __shared__ int sidx[GKL_MAX_ELL];
     __shared__ int snz;
+    __shared__ T red[8][33];
     if (threadIdx.x == 0) {
         int c = 0;
         for (int r = 0; r < fa.nsub; ++r) {
@@ -314,16 +316,26 @@ __global__ void __launch_bounds__(kThreads) k_mv_fin(const T* __restrict__ part,
         snz = c;
     }
     __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int li = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const T* W = static_cast<const T*>(fa.W);
     double sq = 0.0;
-    if (i < n) {
+    for (int64_t i0 = (int64_t)blockIdx.x * 32; i0 < n; i0 += (int64_t)gridDim.x * 32) {
+        const int64_t i = i0 + li;
         T acc = (T)0;
-        for (int c = 0; c < chunks; ++c) acc += part[(int64_t)c * ldp + i];
-        if (s) acc *= (T)s[i];
-        const T* W = static_cast<const T*>(fa.W);
-        for (int q = 0; q < snz; ++q) acc -= (T)sb[q] * W[i + (int64_t)sidx[q] * fa.ldw];
-        y[i] = acc;
-        sq = (double)acc * (double)acc;
+        if (i < n)
+            for (int c = g; c < chunks; c += 8) acc += part[(int64_t)c * ldp + i];
+        red[g][li] = acc;
+        __syncthreads();
+        if (g == 0 && i < n) {
+            T t = red[0][li];
+#pragma unroll
+            for (int q = 1; q < 8; ++q) t += red[q][li];
+            if (s) t *= (T)s[i];
+            for (int q = 0; q < snz; ++q) t -= (T)sb[q] * W[i + (int64_t)sidx[q] * fa.ldw];
+            y[i] = t;
+            sq += (double)t * (double)t;
+        }
+        __syncthreads();
     }
     if (fa.role == ROLE_NONE) return;
     block_sum_to(sq, sv.partials + (int64_t)blockIdx.x * (GKL_MAX_ELL + 2));
@@ -353,8 +365,9 @@ cudaError_t launch_matvec(const gkl_handle* h, const T* v, T* y, void* scratch, 
     Sv s{};
     if (fa) f = *fa;
     if (sv) s = *sv;
-    k_mv_fin<T><<<(unsigned)((h->n + kThreads - 1) / kThreads), kThreads, 0, st>>>(part, p.ldp, p.chunks, h->n, h->s,
-                                                                                   y, f, s);
+    // 32 outputs per block pass; at most 4 blocks per SM (the partial-norm buffer's size)
+    const int fblocks = (int)std::min<int64_t>((h->n + 31) / 32, 4 * (int64_t)h->num_sms);
+    k_mv_fin<T><<<(unsigned)std::max(1, fblocks), 256, 0, st>>>(part, p.ldp, p.chunks, h->n, h->s, y, f, s);
     return cudaGetLastError();
 }
 

@@ -538,30 +538,42 @@ __global__ void __launch_bounds__(256) k_miss_fill(const uint8_t* __restrict__ p
     }
 }
 
-// Missing terms of A^T u for SNP j (one warp per SNP): Z_a, Z_b = sums of z_i over
-// the listed samples of class a (i even) and b (i odd), exact in 64-bit integers;
-// p1[j] -= S 2^-28 (3 Z_a + 4 Z_b), p3[j] += S 2^-28 (Z_a + Z_b) (range-0 partials).
+// Missing terms of A^T u (no cross-block synchronisation): eight lanes per SNP
+// j, four SNPs per warp, eight list entries in flight per lane (the kernel is
+// bound by memory latency times the number of warp waves).  Z_a, Z_b = sums of
+// z_i over the listed samples of class a (i even) and b (i odd), exact in 64-bit
+// integers; p1[j] -= S 2^-28 (3 Z_a + 4 Z_b), p3[j] += S 2^-28 (Z_a + Z_b)
+// (range-0 partials).
 __global__ void __launch_bounds__(256) k_miss_gather(const int64_t* __restrict__ off, const uint32_t* __restrict__ idx,
                                                       int64_t m, const int* __restrict__ z,
                                                       const double* __restrict__ dsc, double* __restrict__ p1,
                                                       double* __restrict__ p3) {
-    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (j >= m) return;
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const int sl = threadIdx.x & 7;
     long long za = 0, zb = 0;
-    for (int64_t e = off[j] + lane; e < off[j + 1]; e += 32) {
-        const uint32_t i = idx[e];
-        const long long v = z[i];
-        if (i & 1u)
-            zb += v;
-        else
-            za += v;
+    if (j < m) {
+        const int64_t e1 = off[j + 1];
+        for (int64_t e = off[j] + sl; e < e1; e += 64) {
+            uint32_t ii[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) ii[u] = e + 8 * u < e1 ? idx[e + 8 * u] : 0xFFFFFFFFu;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (ii[u] != 0xFFFFFFFFu) {
+                    const long long v = z[ii[u]];
+                    if (ii[u] & 1u)
+                        zb += v;
+                    else
+                        za += v;
+                }
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
         za += __shfl_xor_sync(0xffffffffu, za, o);
         zb += __shfl_xor_sync(0xffffffffu, zb, o);
     }
-    if (lane == 0 && (za | zb)) {
+    if (j < m && sl == 0 && (za | zb)) {
         const double zs = ldexp(dsc[0], -28);
         p1[j] -= zs * (double)(3 * za + 4 * zb);
         p3[j] += zs * (double)(za + zb);
@@ -691,7 +703,7 @@ cudaError_t launch_rmatvec_tc(const gkl_handle* h, const float* u, float* x, voi
     if (ev0) cudaEventRecord(ev0, st);
     k_rmv_tc<<<p.grid, kThreads, kSmemBytes, st>>>(map, a);
     if (ev1) cudaEventRecord(ev1, st);
-    k_miss_gather<<<(unsigned)((h->m * 32 + 255) / 256), 256, 0, st>>>(h->miss_off, h->miss_idx, h->m, z, dsc, p1,
+    k_miss_gather<<<(unsigned)((h->m * 8 + 255) / 256), 256, 0, st>>>(h->miss_off, h->miss_idx, h->m, z, dsc, p1,
                                                                        p3);
     FinArgs f{};
     Sv s{};
