@@ -142,6 +142,175 @@ __global__ void k_block_random(float* __restrict__ X, int64_t ldx, int64_t len, 
             if (cols & (1u << j)) X[r + (int64_t)j * ldx] = (float)uniform_pm1(seed, draw + (uint32_t)j, r);
 }
 
+
+// ---- batched block products (every code decoded once for all q vectors) -------
+
+// X[:, 0:q] = A^T U[:, 0:q] (q <= 32), FP32.  A block owns 128 SNPs and all q
+// vectors: thread (pair p, group g) accumulates SNPs 2p, 2p+1 x vectors
+// 8g..8g+7 over all samples, x_{j,c} = d_j w_j sum_i t_j(c_ij) s_i U[i, c] with
+// t_j(c) = c - mu_j (observed), 0 (missing).  Per step the block stages the
+// packed codes of 64 samples (16 bytes of each of its 128 rows) and the 64
+// matching rows of s o U in shared memory.
+__global__ void __launch_bounds__(256) k_block_rmv(const uint8_t* __restrict__ packed, int64_t stride, int64_t n,
+                                                    int64_t m, const double* __restrict__ mu,
+                                                    const double* __restrict__ d, const float* __restrict__ w,
+                                                    const float* __restrict__ s, const float* __restrict__ U,
+                                                    int64_t ldu, int q, float* __restrict__ X, int64_t ldx) {
+    __shared__ __align__(16) uint32_t sc[128][5];   // 16 bytes of codes per row (+ pad)
+    __shared__ __align__(16) float su[64][32];      // s_i U[i, c] (rows 128 B: aligned float4 reads)
+    const int tid = threadIdx.x, pair = tid & 63, g = tid >> 6;
+    const int64_t j0 = (int64_t)blockIdx.x * 128;
+    const int64_t ja = j0 + 2 * pair, jb = ja + 1;
+    const float mua = ja < m ? (float)mu[ja] : 0.f, mub = jb < m ? (float)mu[jb] : 0.f;
+    // per 64-sample step an FP32 partial, added into hi with Kahan compensation lo
+    float acc[2][8], hi[2][8], lo[2][8];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) hi[r][c] = lo[r][c] = 0.f;
+    for (int64_t i0 = 0; i0 < n; i0 += 64) {
+        __syncthreads();
+        // codes: thread t loads 16 bytes of row t/2 (two threads per row, 8 bytes each)
+        {
+            const int row = tid >> 1, half = tid & 1;
+            const int64_t jr = j0 + row, boff = i0 / 4 + 8 * half;
+            uint2 v = make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
+            if (jr < m && boff + 8 <= stride)
+                v = *reinterpret_cast<const uint2*>(packed + jr * stride + boff);
+            sc[row][2 * half] = v.x;
+            sc[row][2 * half + 1] = v.y;
+        }
+        for (int e = tid; e < 64 * 32; e += 256) {
+            const int r = e & 63, c = e >> 6;  // consecutive threads: consecutive samples of one column
+            const int64_t i = i0 + r;
+            float v = 0.f;
+            if (i < n && c < q) v = U[i + (int64_t)c * ldu] * (s ? s[i] : 1.f);
+            su[r][c] = v;
+        }
+        __syncthreads();
+        if (8 * g >= q) continue;
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+#pragma unroll 4
+        for (int wd = 0; wd < 4; ++wd) {
+            const uint32_t wa = sc[2 * pair][wd], wb = sc[2 * pair + 1][wd];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const uint32_t ca = (wa >> (2 * k)) & 3u, cb = (wb >> (2 * k)) & 3u;
+                const float ta = ca == 3u ? 0.f : (float)ca - mua, tb = cb == 3u ? 0.f : (float)cb - mub;
+                const float4 u0 = *reinterpret_cast<const float4*>(&su[16 * wd + k][8 * g]);
+                const float4 u1 = *reinterpret_cast<const float4*>(&su[16 * wd + k][8 * g + 4]);
+                const float uu[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    acc[0][c] = fmaf(ta, uu[c], acc[0][c]);
+                    acc[1][c] = fmaf(tb, uu[c], acc[1][c]);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float y = acc[r][c] - lo[r][c], t = hi[r][c] + y;
+                lo[r][c] = (t - hi[r][c]) - y;
+                hi[r][c] = t;
+            }
+    }
+    const int64_t jj[2] = {ja, jb};
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        if (jj[r] >= m) continue;
+        double dw = d[jj[r]];
+        if (w) dw *= (double)w[jj[r]];
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (8 * g + c < q) X[jj[r] + (int64_t)(8 * g + c) * ldx] = (float)(dw * ((double)hi[r][c] - (double)lo[r][c]));
+    }
+}
+
+// Partials of Y = A V (V m x q, q <= 32) over SNP chunk blockIdx.y: thread
+// (group p, vector group g) owns samples 8p..8p+7 of the block's 512 and
+// vectors 8g..8g+7; part[chunk][c][i] = sum_{j in chunk} t_j(c_ij) V[j, c] with
+// t_j(c) = (c - mu_j) d_j w_j (observed), 0 (missing).  V rows and the per-SNP
+// coefficients are staged 64 SNPs at a time.
+__global__ void __launch_bounds__(256) k_block_mv_part(const uint8_t* __restrict__ packed, int64_t stride, int64_t n,
+                                                        int64_t m, int64_t rpc, const double* __restrict__ mu,
+                                                        const double* __restrict__ d, const float* __restrict__ w,
+                                                        const float* __restrict__ V, int64_t ldv, int q,
+                                                        float* __restrict__ part, int64_t ldp) {
+    __shared__ __align__(16) float sv[64][32];  // rows 128 B: aligned float4 reads
+    __shared__ float sa[64], sb[64];  // t = code * sa - sb for observed codes
+    const int tid = threadIdx.x, p = tid & 63, g = tid >> 6;
+    const int64_t i0 = (int64_t)blockIdx.x * 512 + 8 * p;  // first of this thread's 8 samples
+    const int64_t j0 = (int64_t)blockIdx.y * rpc, j1 = min(m, j0 + rpc);
+    float acc[8][8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[k][c] = 0.f;
+    for (int64_t jb = j0; jb < j1; jb += 64) {
+        const int nr = (int)min((int64_t)64, j1 - jb);
+        __syncthreads();
+        for (int e = tid; e < 64 * 32; e += 256) {
+            const int r = e & 63, c = e >> 6;  // consecutive threads: consecutive SNPs of one column
+            sv[r][c] = (r < nr && c < q) ? V[(jb + r) + (int64_t)c * ldv] : 0.f;
+        }
+        if (tid < 64) {
+            float a = 0.f, b = 0.f;
+            if (tid < nr) {
+                double dw = d[jb + tid];
+                if (w) dw *= (double)w[jb + tid];
+                a = (float)dw;
+                b = (float)(mu[jb + tid] * dw);
+            }
+            sa[tid] = a;
+            sb[tid] = b;
+        }
+        __syncthreads();
+        if (8 * g >= q) continue;
+        for (int r = 0; r < nr; ++r) {
+            const int64_t boff = (jb + r) * stride + i0 / 4;
+            const uint32_t cw = (i0 < n && i0 / 4 + 2 <= stride) ? (uint32_t)__ldg(reinterpret_cast<const unsigned short*>(packed + boff))
+                                                                 : 0xFFFFu;
+            const float a = sa[r], b = sb[r];
+            const float4 v0 = *reinterpret_cast<const float4*>(&sv[r][8 * g]);
+            const float4 v1 = *reinterpret_cast<const float4*>(&sv[r][8 * g + 4]);
+            const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uint32_t cd = (cw >> (2 * k)) & 3u;
+                const float t = cd == 3u ? 0.f : fmaf((float)cd, a, -b);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[k][c] = fmaf(t, vv[c], acc[k][c]);
+            }
+        }
+    }
+    if (8 * g >= q) return;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        if (8 * g + c >= q) break;
+        float* out = part + (int64_t)blockIdx.y * ldp * q + (int64_t)(8 * g + c) * ldp;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (i0 + k < n) out[i0 + k] = acc[k][c];
+    }
+}
+
+// Y[i, c] = s_i sum_chunk part[chunk][c][i] (fixed order).
+__global__ void k_block_mv_fin(const float* __restrict__ part, int64_t ldp, int chunks, int64_t n, int q,
+                               const float* __restrict__ s, float* __restrict__ Y, int64_t ldy) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * q) return;
+    const int64_t i = e % n, c = e / n;
+    float t = 0.f;
+    for (int ch = 0; ch < chunks; ++ch) t += part[(int64_t)ch * ldp * q + c * ldp + i];
+    if (s) t *= s[i];
+    Y[i + c * ldy] = t;
+}
+
 // ---- host linear algebra (b x b, FP64) -----------------------------------------
 
 // Symmetric eigen-decomposition by cyclic Jacobi: G = Z diag(lam) Z^T.
@@ -231,6 +400,7 @@ struct BlockCtx {
     cudaStream_t st;
     double* d_part;    // Gram partials
     double* d_small;   // p x q FP64 results / coefficient uploads
+    float* d_bpart;    // A V partials of the batched product
     int nblk_max;
     uint64_t seed;
     uint32_t draw;
@@ -366,22 +536,39 @@ static cudaError_t orthonormalize_once(BlockCtx& c, float* X, int64_t ldx, int q
     return cudaGetLastError();
 }
 
-// Y[:, 0:q] = A X[:, 0:q] (forward) or A^T X (transpose), one column at a time
-// with the single-vector kernels.
+// Y[:, 0:q] = A X[:, 0:q] (forward) or A^T X (transpose) with the batched kernels.
+constexpr size_t kBlockPartBytes = 64u << 20;  // A V partials (chunks x q x n floats)
+
+static void mv_chunks(const gkl_handle* h, int q, int& tiles, int& chunks, int64_t& rpc, int64_t& ldp) {
+    tiles = (int)((h->n + 511) / 512);
+    ldp = (h->n + 31) / 32 * 32;
+    const int64_t cap = std::max<int64_t>(1, (int64_t)(kBlockPartBytes / (sizeof(float) * (size_t)q * (size_t)ldp)));
+    const int64_t want = std::max<int64_t>(1, (4 * (int64_t)h->num_sms + tiles - 1) / tiles);
+    int64_t ch = std::min<int64_t>({want, cap, (h->m + 63) / 64});
+    rpc = (h->m + ch - 1) / ch;
+    rpc = (rpc + 63) / 64 * 64;
+    chunks = (int)((h->m + rpc - 1) / rpc);
+}
+
 static cudaError_t block_product(BlockCtx& c, bool transpose, const float* X, int64_t ldx, float* Y, int64_t ldy,
                                  int q) {
     gkl_handle* h = c.h;
-    for (int j = 0; j < q; ++j) {
-        int nl = 0;
-        cudaError_t e = transpose ? launch_rmatvec<float>(h, X + (int64_t)j * ldx, Y + (int64_t)j * ldy, h->scratch,
-                                                          nullptr, nullptr, nullptr, nullptr, &nl)
-                                  : launch_matvec<float>(h, X + (int64_t)j * ldx, Y + (int64_t)j * ldy, h->scratch,
-                                                         nullptr, nullptr, nullptr, nullptr, &nl);
-        if (e != cudaSuccess) return e;
-        c.launches += nl;
+    if (transpose) {
+        k_block_rmv<<<(unsigned)((h->m + 127) / 128), 256, 0, c.st>>>(h->packed, h->stride, h->n, h->m, h->mu, h->d,
+                                                                        h->w, h->s, X, ldx, q, Y, ldy);
+        c.launches += 1;
+    } else {
+        int tiles, chunks;
+        int64_t rpc, ldp;
+        mv_chunks(h, q, tiles, chunks, rpc, ldp);
+        k_block_mv_part<<<dim3((unsigned)tiles, (unsigned)chunks), 256, 0, c.st>>>(
+            h->packed, h->stride, h->n, h->m, rpc, h->mu, h->d, h->w, X, ldx, q, c.d_bpart, ldp);
+        k_block_mv_fin<<<(unsigned)((h->n * q + 255) / 256), 256, 0, c.st>>>(c.d_bpart, ldp, chunks, h->n, q, h->s, Y,
+                                                                              ldy);
+        c.launches += 2;
+        c.products += q;
     }
-    c.products += transpose ? 0 : q;
-    return cudaSuccess;
+    return cudaGetLastError();
 }
 
 static int64_t round32(int64_t x) { return (x + 31) / 32 * 32; }
@@ -401,9 +588,6 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
     if (kk < k || kk >= ell || (ell - kk) % b != 0)
         return set_err(h, GKL_ERR_ARG, "k_keep must satisfy k <= k_keep < ell with ell - k_keep a multiple of b");
     if (!(o->tol > 0.0) || o->maxit < 1) return set_err(h, GKL_ERR_ARG, "tol must be > 0 and maxit >= 1");
-    MvPlan plan = plan_products(h);
-    int st = ensure_scratch(h, plan.bytes_fp64);
-    if (st) return st;
     const int64_t ldu = round32(n), ldv = round32(m);
     const size_t ell2 = (size_t)ell * ell;
     const int nblk = 4 * h->num_sms;
@@ -422,6 +606,10 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
     const size_t oPart = take(sizeof(double) * (size_t)nblk * GKL_MAX_ELL * kMaxB),
                  oSmall = take(sizeof(double) * GKL_MAX_ELL * kMaxB), oSigns = take(sizeof(int) * GKL_MAX_ELL);
     const size_t oOutU = take(sizeof(float) * n * k), oOutV = take(sizeof(float) * m * k);
+    int mvt, mvc;
+    int64_t mvr, mvl;
+    mv_chunks(h, b, mvt, mvc, mvr, mvl);
+    const size_t oBpart = take(sizeof(float) * (size_t)mvc * (size_t)b * (size_t)mvl);
     void* ws = nullptr;
     if (cudaMalloc(&ws, off) != cudaSuccess) return set_err(h, GKL_ERR_CUDA, "block workspace of %zu bytes", off);
     char* W = static_cast<char*>(ws);
@@ -446,8 +634,8 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
     sv.co = reinterpret_cast<CycleOut*>(W + oCo);
     sv.eps_w = 5.9604644775390625e-08;
     sv.tol = o->tol;
-    BlockCtx c{h, h->stream, reinterpret_cast<double*>(W + oPart), reinterpret_cast<double*>(W + oSmall), nblk,
-               o->seed, 0x42000000u, 0, 0, 0.0, 0.0, 0};
+    BlockCtx c{h, h->stream, reinterpret_cast<double*>(W + oPart), reinterpret_cast<double*>(W + oSmall),
+               reinterpret_cast<float*>(W + oBpart), nblk, o->seed, 0x42000000u, 0, 0, 0.0, 0.0, 0};
     cudaError_t e = cudaMemsetAsync(sv.sc, 0, sizeof(DevScal), c.st);
     cudaEvent_t ev0, ev1;
     cudaEventCreate(&ev0);
