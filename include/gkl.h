@@ -149,6 +149,23 @@ int gkl_matvec(gkl_handle* h, int prec, const void* v, void* y);
 /* x = A^T u.  prec as for gkl_matvec; u (device, n entries), x (device, m). */
 int gkl_rmatvec(gkl_handle* h, int prec, const void* u, void* x);
 
+/* Block products of the block form on the tensor cores (tcgen05):
+ *   transpose = 0:  Y (n x q) = A X,    X (m x q)
+ *   transpose = 1:  Y (m x q) = A^T X,  X (n x q)
+ * X, Y: device FP32, column-major with leading dimensions ldx, ldy (>= rows).
+ * q: 1..32 vectors.  digits: 8 (each vector in 32-bit fixed point relative to
+ *   its largest entry: finer than the FP32 input) or 4 (16-bit fixed point,
+ *   the precision of a split hi+lo BF16 pair).  The genotypes are exact on the
+ *   tensor cores and the accumulation is exact; the one rounding per entry is
+ *   the fixed-point representation of the input block (|dx| <= 2^-(4 digits+1)
+ *   of its largest entry) plus the final rounding to FP32.
+ * Allocates its scratch per call (digit tiles, partial sums) and synchronises
+ * the stream.  GKL_ERR_ARG if the tensor-core path is unavailable for this
+ * handle (packed buffer not 16-byte aligned, or n > 524,000) or arguments are
+ * out of range; GKL_ERR_CUDA on a CUDA error or a pipeline wait that ran out. */
+int gkl_matmat(gkl_handle* h, int32_t transpose, int32_t q, int32_t digits, const float* X, int64_t ldx, float* Y,
+               int64_t ldy);
+
 /* y = A v, allocating no device memory (no handle needed).  The paper has no
  * counterpart: this is for callers that may not call cudaMalloc -- code whose
  * device memory is owned by a host application's own pool or arena, or loops

@@ -24,6 +24,7 @@
 // X_before = X_after R is accumulated in FP64.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -33,20 +34,24 @@
 namespace gkl {
 
 namespace {
-constexpr int kGramRows = 64;   // rows per FP32 partial sum
+constexpr int kGramRows = 32;   // rows per FP32 partial sum
 constexpr int kMaxB = 32;       // block size limit (Gram kernel tile)
 }
 
 // ---- kernels ------------------------------------------------------------------
 
 // part[blk][i + p j] = sum over the block's rows r of X[r + i ldx] Y[r + j ldy]
-// (i < p <= 128, j < q <= 32): FP32 products over 64 rows, FP64 across.
+// (i < p <= 128, j < q <= 32): FP32 products summed over 32-row chunks, the
+// chunk sums added in FP64.  Each chunk is loaded into registers while the
+// previous one is multiplied out of shared memory (two buffers, one barrier
+// per chunk).
 __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ X, int64_t ldx, int p,
                                                     const float* __restrict__ Y, int64_t ldy, int q, int64_t len,
                                                     int64_t rows_per_blk, double* __restrict__ part) {
-    __shared__ float sx[kGramRows][129];
-    __shared__ float sy[kGramRows][33];
+    __shared__ float sx[2][kGramRows][129];
+    __shared__ float sy[2][kGramRows][33];
     const int t = threadIdx.x, gi = t & 31, gj = t >> 5;
+    const int lr = t & 31, lc = t >> 5;  // load role: row lr, columns lc + 8 k
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_blk;
     const int64_t r1 = min(len, r0 + rows_per_blk);
     double acc[4][4];
@@ -54,28 +59,42 @@ __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ X, 
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[a][c] = 0.0;
-    for (int64_t rb = r0; rb < r1; rb += kGramRows) {
-        const int nr = (int)min((int64_t)kGramRows, r1 - rb);
-        for (int idx = t; idx < kGramRows * p; idx += 256) {
-            const int rr = idx % kGramRows, c = idx / kGramRows;
-            sx[rr][c] = rr < nr ? X[(rb + rr) + (int64_t)c * ldx] : 0.f;
+    float xr[16], yr[4];
+    auto load = [&](int64_t rb) {
+        const int64_t r = rb + lr;
+        const bool ok = r < r1;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int c = lc + 8 * k;
+            xr[k] = (ok && c < p) ? X[r + (int64_t)c * ldx] : 0.f;
         }
-        for (int idx = t; idx < kGramRows * q; idx += 256) {
-            const int rr = idx % kGramRows, c = idx / kGramRows;
-            sy[rr][c] = rr < nr ? Y[(rb + rr) + (int64_t)c * ldy] : 0.f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c = lc + 8 * k;
+            yr[k] = (ok && c < q) ? Y[r + (int64_t)c * ldy] : 0.f;
         }
+    };
+    if (r0 < r1) load(r0);
+    int buf = 0;
+    for (int64_t rb = r0; rb < r1; rb += kGramRows, buf ^= 1) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) sx[buf][lr][lc + 8 * k] = xr[k];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sy[buf][lr][lc + 8 * k] = yr[k];
         __syncthreads();
+        if (rb + kGramRows < r1) load(rb + kGramRows);
         float f[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int c = 0; c < 4; ++c) f[a][c] = 0.f;
-        for (int rr = 0; rr < nr; ++rr) {
+#pragma unroll 8
+        for (int rr = 0; rr < kGramRows; ++rr) {
             float xa[4], yc[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) xa[a] = (gi + 32 * a < p) ? sx[rr][gi + 32 * a] : 0.f;
+            for (int a = 0; a < 4; ++a) xa[a] = sx[buf][rr][gi + 32 * a];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) yc[c] = (gj + 8 * c < q) ? sy[rr][gj + 8 * c] : 0.f;
+            for (int c = 0; c < 4; ++c) yc[c] = sy[buf][rr][gj + 8 * c];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -85,7 +104,6 @@ __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ X, 
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int c = 0; c < 4; ++c) acc[a][c] += (double)f[a][c];
-        __syncthreads();
     }
     double* out = part + (int64_t)blockIdx.x * p * q;
 #pragma unroll
@@ -97,32 +115,57 @@ __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ X, 
         }
 }
 
-// out[e] = sum_blk part[blk][e] in block order (deterministic).
-__global__ void k_gram_sum(const double* __restrict__ part, int nblk, int pq, double* __restrict__ out) {
+// out[e] = sum_blk part[blk][e] in block order (deterministic); eight loads in flight.
+__global__ void __launch_bounds__(64) k_gram_sum(const double* __restrict__ part, int nblk, int pq,
+                                                 double* __restrict__ out) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= pq) return;
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * pq + e];
+    int b = 0;
+    for (; b + 8 <= nblk; b += 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = part[(int64_t)(b + u) * pq + e];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; b < nblk; ++b) s += part[(int64_t)b * pq + e];
     out[e] = s;
 }
 
 // X[:, 0:q] <- alpha X[:, 0:q] + beta Y[:, 0:p] C  (C p x q, FP64, column-major), per row.
-// X and Y may be the same buffer only with alpha = 0 (X <- beta X C).
+// X and Y may be the same buffer only with alpha = 0 (X <- beta X C).  C is
+// held row by row in shared memory (FP32, 32 columns) and read as float4.
 __global__ void __launch_bounds__(256) k_block_axpy(float* X, int64_t ldx, int q, const float* Y,
                                                      int64_t ldy, int p, const double* __restrict__ C, float alpha,
                                                      float beta, int64_t len) {
-    __shared__ float sc[128 * kMaxB];
-    for (int e = threadIdx.x; e < p * q; e += blockDim.x) sc[e] = (float)C[e];
+    __shared__ __align__(16) float sc[128 * kMaxB];
+    for (int e = threadIdx.x; e < p * kMaxB; e += blockDim.x) {
+        const int i = e / kMaxB, j = e % kMaxB;
+        sc[e] = j < q ? (float)C[i + p * j] : 0.f;
+    }
     __syncthreads();
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < len; r += (int64_t)gridDim.x * blockDim.x) {
         float acc[kMaxB];
 #pragma unroll
         for (int j = 0; j < kMaxB; ++j) acc[j] = 0.f;
-        for (int i = 0; i < p; ++i) {
-            const float y = Y[r + (int64_t)i * ldy];
+        for (int i0 = 0; i0 < p; i0 += 4) {
+            float y[4];
 #pragma unroll
-            for (int j = 0; j < kMaxB; ++j)
-                if (j < q) acc[j] = fmaf(y, sc[i + p * j], acc[j]);
+            for (int u = 0; u < 4; ++u) y[u] = i0 + u < p ? Y[r + (int64_t)(i0 + u) * ldy] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (i0 + u >= p) break;
+                const float4* cr = reinterpret_cast<const float4*>(sc + (i0 + u) * kMaxB);
+#pragma unroll
+                for (int j4 = 0; j4 < kMaxB / 4; ++j4) {
+                    const float4 cv = cr[j4];
+                    acc[4 * j4] = fmaf(y[u], cv.x, acc[4 * j4]);
+                    acc[4 * j4 + 1] = fmaf(y[u], cv.y, acc[4 * j4 + 1]);
+                    acc[4 * j4 + 2] = fmaf(y[u], cv.z, acc[4 * j4 + 2]);
+                    acc[4 * j4 + 3] = fmaf(y[u], cv.w, acc[4 * j4 + 3]);
+                }
+            }
         }
 #pragma unroll
         for (int j = 0; j < kMaxB; ++j)
@@ -401,6 +444,8 @@ struct BlockCtx {
     double* d_part;    // Gram partials
     double* d_small;   // p x q FP64 results / coefficient uploads
     float* d_bpart;    // A V partials of the batched product
+    void* tc_scratch;  // tensor-core products: digit tiles, partials (null: SIMT kernels)
+    int tc_digits;     // digits per vector of the tensor-core products
     int nblk_max;
     uint64_t seed;
     uint32_t draw;
@@ -411,7 +456,8 @@ struct BlockCtx {
 };
 
 static int gram_blocks(const BlockCtx& c, int64_t len) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(c.nblk_max, (len + 1023) / 1024));
+    // two resident blocks per SM (registers), at least 256 rows each
+    return (int)std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)c.h->num_sms, (len + 255) / 256));
 }
 
 // C (p x q, device FP64) = X^T Y
@@ -420,7 +466,7 @@ static cudaError_t gram(BlockCtx& c, const float* X, int64_t ldx, int p, const f
     const int nb = gram_blocks(c, len);
     const int64_t rpb = (len + nb - 1) / nb;
     k_gram_part<<<nb, 256, 0, c.st>>>(X, ldx, p, Y, ldy, q, len, rpb, c.d_part);
-    k_gram_sum<<<(p * q + 255) / 256, 256, 0, c.st>>>(c.d_part, nb, p * q, C);
+    k_gram_sum<<<(p * q + 63) / 64, 64, 0, c.st>>>(c.d_part, nb, p * q, C);
     c.launches += 2;
     return cudaGetLastError();
 }
@@ -553,6 +599,19 @@ static void mv_chunks(const gkl_handle* h, int q, int& tiles, int& chunks, int64
 static cudaError_t block_product(BlockCtx& c, bool transpose, const float* X, int64_t ldx, float* Y, int64_t ldy,
                                  int q) {
     gkl_handle* h = c.h;
+    if (c.tc_scratch) {
+        // tensor cores: at most 128 / D vectors per pass
+        const int per = 128 / c.tc_digits;
+        for (int c0 = 0; c0 < q; c0 += per) {
+            int nl = 0;
+            cudaError_t e = launch_block_product_tc(h, transpose, X + (int64_t)c0 * ldx, ldx, std::min(per, q - c0),
+                                                    c.tc_digits, Y + (int64_t)c0 * ldy, ldy, c.tc_scratch, &nl);
+            if (e != cudaSuccess) return e;
+            c.launches += nl;
+        }
+        if (!transpose) c.products += q;
+        return cudaSuccess;
+    }
     if (transpose) {
         k_block_rmv<<<(unsigned)((h->m + 127) / 128), 256, 0, c.st>>>(h->packed, h->stride, h->n, h->m, h->mu, h->d,
                                                                         h->w, h->s, X, ldx, q, Y, ldy);
@@ -606,10 +665,16 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
     const size_t oPart = take(sizeof(double) * (size_t)nblk * GKL_MAX_ELL * kMaxB),
                  oSmall = take(sizeof(double) * GKL_MAX_ELL * kMaxB), oSigns = take(sizeof(int) * GKL_MAX_ELL);
     const size_t oOutU = take(sizeof(float) * n * k), oOutV = take(sizeof(float) * m * k);
+    // products: tcgen05 with 8 digits per vector (finer than FP32) where the
+    // handle supports it (GKL_BLOCK_PRODUCTS=simt selects the SIMT kernels)
+    const char* bpk = getenv("GKL_BLOCK_PRODUCTS");
+    const bool use_tc = !(bpk && strcmp(bpk, "simt") == 0) && block_tc_prepare(h);
+    const int tc_digits = 8;
     int mvt, mvc;
     int64_t mvr, mvl;
     mv_chunks(h, b, mvt, mvc, mvr, mvl);
-    const size_t oBpart = take(sizeof(float) * (size_t)mvc * (size_t)b * (size_t)mvl);
+    const size_t oBpart = use_tc ? take(block_tc_scratch_bytes(h, 128 / tc_digits))
+                                 : take(sizeof(float) * (size_t)mvc * (size_t)b * (size_t)mvl);
     void* ws = nullptr;
     if (cudaMalloc(&ws, off) != cudaSuccess) return set_err(h, GKL_ERR_CUDA, "block workspace of %zu bytes", off);
     char* W = static_cast<char*>(ws);
@@ -623,9 +688,10 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
     sv.ldu = ldu;
     sv.ldv = ldv;
     sv.ell = ell;
-    sv.kk = kk;
+    sv.kk = k;  // the projected SVD refines (and checks) the k wanted triplets
     sv.k = k;
     sv.prec = GKL_FP32;
+    sv.fp32_only = 1;
     sv.B = reinterpret_cast<double*>(W + oT);
     sv.P = reinterpret_cast<double*>(W + oP);
     sv.Q = reinterpret_cast<double*>(W + oQ);
@@ -634,8 +700,21 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
     sv.co = reinterpret_cast<CycleOut*>(W + oCo);
     sv.eps_w = 5.9604644775390625e-08;
     sv.tol = o->tol;
-    BlockCtx c{h, h->stream, reinterpret_cast<double*>(W + oPart), reinterpret_cast<double*>(W + oSmall),
-               reinterpret_cast<float*>(W + oBpart), nblk, o->seed, 0x42000000u, 0, 0, 0.0, 0.0, 0};
+    BlockCtx c{h,
+               h->stream,
+               reinterpret_cast<double*>(W + oPart),
+               reinterpret_cast<double*>(W + oSmall),
+               use_tc ? nullptr : reinterpret_cast<float*>(W + oBpart),
+               use_tc ? static_cast<void*>(W + oBpart) : nullptr,
+               tc_digits,
+               nblk,
+               o->seed,
+               0x42000000u,
+               0,
+               0,
+               0.0,
+               0.0,
+               0};
     cudaError_t e = cudaMemsetAsync(sv.sc, 0, sizeof(DevScal), c.st);
     cudaEvent_t ev0, ev1;
     cudaEventCreate(&ev0);
@@ -644,7 +723,7 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
     std::vector<double> T(ell2, 0.0), R, S, P, sg;
     std::vector<double> Slast;
     CycleOut* ho = h->host_out;
-    int cycle = 0, restarts = 0, converged = 0;
+    int cycle = 0, restarts = 0, converged = 0, svd_fb = 0, svd_fp64 = 0, max_sweeps = 0;
     double maxrel = 0.0, dtheta = 0.0;
     std::vector<double> res(k, 0.0);
     auto fail = [&](const char* what) {
@@ -699,33 +778,52 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
                 Slast = S;
             }
         }
-        // projected SVD of T (FP32 Jacobi + FP64 refinement, FP64 fallback)
-        if ((e = upload(c, T, sv.B)) != cudaSuccess) return fail("T upload");
-        if ((e = launch_small_svd(sv, c.st, 0)) != cudaSuccess) return fail("projected SVD");
-        c.launches += 10;
-        e = cudaMemcpyAsync(ho, sv.co, sizeof(CycleOut), cudaMemcpyDeviceToHost, c.st);
-        if (e == cudaSuccess) e = download(c, sv.P, P, ell2);
-        if (e != cudaSuccess) return fail("projected SVD results");
-        sg.assign(ho->sg, ho->sg + ell);
-        // block residuals r_i = || S_last P[ell-b:ell, i] ||
+        // projected SVD of T: FP32 Jacobi, FP64 refinement of the k wanted
+        // triplets; where that refinement does not apply (clustered values)
+        // the FP32 triplets serve the restart, and the last cycle repeats the
+        // SVD with the FP64 Jacobi
         double mx = 0.0, sum = 0.0;
         std::vector<double> SP((size_t)b * ell);
-        for (int i = 0; i < ell; ++i)
-            for (int r = 0; r < b; ++r) {
+        auto projected = [&](bool fp64_fallback) -> cudaError_t {
+            sv.fp32_only = fp64_fallback ? 0 : 1;
+            cudaError_t err = launch_small_svd(sv, c.st, 0);
+            sv.fp32_only = 1;
+            if (err != cudaSuccess) return err;
+            c.launches += 10;
+            err = cudaMemcpyAsync(ho, sv.co, sizeof(CycleOut), cudaMemcpyDeviceToHost, c.st);
+            if (err == cudaSuccess)
+                err = cudaMemcpyAsync(&svd_fb, &sv.sc->svd_fallback, sizeof(int), cudaMemcpyDeviceToHost, c.st);
+            if (err == cudaSuccess) err = download(c, sv.P, P, ell2);
+            if (err != cudaSuccess) return err;
+            sg.assign(ho->sg, ho->sg + ell);
+            max_sweeps = std::max(max_sweeps, ho->sweeps);
+            // block residuals r_i = || S_last P[ell-b:ell, i] ||
+            mx = 0.0;
+            sum = 0.0;
+            for (int i = 0; i < ell; ++i)
+                for (int r = 0; r < b; ++r) {
+                    double a = 0.0;
+                    for (int t = 0; t < b; ++t) a += Slast[r + (size_t)b * t] * P[(ell - b + t) + (size_t)ell * i];
+                    SP[r + (size_t)b * i] = a;
+                }
+            for (int i = 0; i < k; ++i) {
                 double a = 0.0;
-                for (int t = 0; t < b; ++t) a += Slast[r + (size_t)b * t] * P[(ell - b + t) + (size_t)ell * i];
-                SP[r + (size_t)b * i] = a;
+                for (int r = 0; r < b; ++r) a += SP[r + (size_t)b * i] * SP[r + (size_t)b * i];
+                res[i] = std::sqrt(a);
+                mx = std::max(mx, res[i]);
+                sum += res[i];
             }
-        for (int i = 0; i < k; ++i) {
-            double a = 0.0;
-            for (int r = 0; r < b; ++r) a += SP[r + (size_t)b * i] * SP[r + (size_t)b * i];
-            res[i] = std::sqrt(a);
-            mx = std::max(mx, res[i]);
-            sum += res[i];
+            maxrel = sg[0] > 0.0 ? mx / sg[0] : 0.0;
+            dtheta = sum;
+            converged = mx <= o->tol * sg[0] || sg[0] == 0.0;
+            return cudaSuccess;
+        };
+        if ((e = upload(c, T, sv.B)) != cudaSuccess) return fail("T upload");
+        if ((e = projected(false)) != cudaSuccess) return fail("projected SVD");
+        if ((converged || cycle == o->maxit - 1) && svd_fb) {
+            ++svd_fp64;
+            if ((e = projected(true)) != cudaSuccess) return fail("projected SVD (FP64)");
         }
-        maxrel = sg[0] > 0.0 ? mx / sg[0] : 0.0;
-        dtheta = sum;
-        converged = mx <= o->tol * sg[0] || sg[0] == 0.0;
         if (converged || cycle == o->maxit - 1) break;
         // thick restart: keep kk Ritz vectors, spike block from S_last
         e = launch_rotate<float>(c.st, U, ldu, ell, sv.P, ell, kk, U2, ldu, n);
@@ -744,17 +842,89 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
         }
         ++restarts;
     }
-    // output: U P[:, :k], V Q[:, :k], sign rule, copy-out
+    // output: U P[:, :k], V Q[:, :k]; for k <= 32 refined by one Rayleigh-Ritz
+    // step on span(V Q[:, :k]) with FP32-grade products (W = A V_k, W^T W = Y
+    // Lambda Y^T in FP64, sigma = sqrt(lambda), V = V_k Y, U = W Y / sigma),
+    // whose singular values are accurate to the square of the subspace angle,
+    // and the true residuals ||A^T u_i - sigma_i v_i|| from one more product
     float* Uo = reinterpret_cast<float*>(W + oOutU);
     float* Vo = reinterpret_cast<float*>(W + oOutV);
-    e = launch_rotate<float>(c.st, U, ldu, ell, sv.P, ell, k, Uo, n, n);
-    if (e == cudaSuccess) e = launch_rotate<float>(c.st, V, ldv, ell, sv.Q, ell, k, Vo, m, m);
+    if (k <= kMaxB) {
+        float* Vk = V2;  // m x k (ldv)
+        float* Wk = U2;  // n x k (ldu)
+        std::vector<double> G, lam, Y, Rk;
+        e = launch_rotate<float>(c.st, V, ldv, ell, sv.Q, ell, k, Vk, ldv, m);
+        if (e == cudaSuccess) e = orthonormalize(c, Vk, ldv, k, nullptr, ldv, 0, m, Rk);
+        if (e == cudaSuccess) e = block_product(c, false, Vk, ldv, Wk, ldu, k);
+        if (e == cudaSuccess) e = gram(c, Wk, ldu, k, Wk, ldu, k, n, c.d_small);
+        if (e == cudaSuccess) e = download(c, c.d_small, G, (size_t)k * k);
+        if (e != cudaSuccess) return fail("Rayleigh-Ritz step");
+        sym_eig(k, G, lam, Y);
+        std::vector<int> ord(k);
+        for (int i = 0; i < k; ++i) ord[i] = i;
+        std::sort(ord.begin(), ord.end(), [&](int a, int b2) { return lam[a] > lam[b2]; });
+        std::vector<double> Cv((size_t)k * k), Cu((size_t)k * k), Cs((size_t)k * k, 0.0);
+        for (int j = 0; j < k; ++j) {
+            const double sj = std::sqrt(std::max(0.0, lam[ord[j]]));
+            sg[j] = sj;
+            for (int r = 0; r < k; ++r) {
+                Cv[r + (size_t)k * j] = Y[r + (size_t)k * ord[j]];
+                Cu[r + (size_t)k * j] = sj > 0.0 ? Y[r + (size_t)k * ord[j]] / sj : 0.0;
+            }
+            Cs[j + (size_t)k * j] = sj;
+        }
+        e = upload(c, Cv, c.d_small);
+        if (e == cudaSuccess) {
+            k_block_axpy<<<axpy_grid(c, m), 256, 0, c.st>>>(Vo, m, k, Vk, ldv, k, c.d_small, 0.f, 1.f, m);
+            e = cudaStreamSynchronize(c.st);  // d_small is reused below
+        }
+        if (e == cudaSuccess) e = upload(c, Cu, c.d_small);
+        if (e == cudaSuccess) {
+            k_block_axpy<<<axpy_grid(c, n), 256, 0, c.st>>>(Uo, n, k, Wk, ldu, k, c.d_small, 0.f, 1.f, n);
+            e = cudaStreamSynchronize(c.st);
+        }
+        // true residuals: Z = A^T U - V diag(sigma), r_i = ||Z_i||
+        if (e == cudaSuccess) e = block_product(c, true, Uo, n, Vk, ldv, k);
+        if (e == cudaSuccess) e = upload(c, Cs, c.d_small);
+        if (e == cudaSuccess) {
+            k_block_axpy<<<axpy_grid(c, m), 256, 0, c.st>>>(Vk, ldv, k, Vo, m, k, c.d_small, 1.f, -1.f, m);
+            e = cudaStreamSynchronize(c.st);
+        }
+        if (e == cudaSuccess) e = gram(c, Vk, ldv, k, Vk, ldv, k, m, c.d_small);
+        if (e == cudaSuccess) e = download(c, c.d_small, G, (size_t)k * k);
+        if (e != cudaSuccess) return fail("Rayleigh-Ritz step");
+        c.launches += 3;
+        double mxr = 0.0, sumr = 0.0;
+        for (int i = 0; i < k; ++i) {
+            res[i] = std::sqrt(std::max(0.0, G[i + (size_t)k * i]));
+            mxr = std::max(mxr, res[i]);
+            sumr += res[i];
+        }
+        maxrel = sg[0] > 0.0 ? mxr / sg[0] : 0.0;
+        dtheta = sumr;
+    } else {
+        e = launch_rotate<float>(c.st, U, ldu, ell, sv.P, ell, k, Uo, n, n);
+        if (e == cudaSuccess) e = launch_rotate<float>(c.st, V, ldv, ell, sv.Q, ell, k, Vo, m, m);
+    }
     if (e == cudaSuccess) e = launch_sign_fix<float>(c.st, Uo, n, Vo, m, k, reinterpret_cast<int*>(W + oSigns));
     if (e == cudaSuccess && Uout) e = cudaMemcpyAsync(Uout, Uo, sizeof(float) * n * k, cudaMemcpyDeviceToDevice, c.st);
     if (e == cudaSuccess && Vout) e = cudaMemcpyAsync(Vout, Vo, sizeof(float) * m * k, cudaMemcpyDeviceToDevice, c.st);
     cudaEventRecord(ev1, c.st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
     if (e != cudaSuccess) return fail("output");
+    if (use_tc) {
+        int terr = 0;
+        int* ew = reinterpret_cast<int*>(reinterpret_cast<char*>(h->aux) + kAuxErrOffset);
+        e = cudaMemcpy(&terr, ew, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return fail("error word");
+        if (terr) {
+            cudaMemset(ew, 0, sizeof(int));
+            cudaFree(ws);
+            cudaEventDestroy(ev0);
+            cudaEventDestroy(ev1);
+            return set_err(h, GKL_ERR_CUDA, "tensor-core block product: a pipeline wait ran out (code %d)", terr);
+        }
+    }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev0, ev1);
     for (int i = 0; i < k; ++i) {
@@ -772,6 +942,8 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
         info->dtheta1 = dtheta;
         info->ms_total = ms;
         info->launches = c.launches + 5;
+        info->svd_fallbacks = svd_fp64;
+        info->jacobi_sweeps = max_sweeps;
     }
     h->last_valid = 0;  // gkl_grad works from the single-vector solvers' triplets
     cudaFree(ws);

@@ -50,6 +50,7 @@ struct Sv {
     int ell, kk, k, reorth;
     int kk_start;             // first step of the current cycle (0, or kk after a restart)
     int prec;                 // GKL_FP64 / GKL_FP32
+    int fp32_only;            // projected SVD: no FP64 Jacobi fallback (block form)
     void* U;                  // n x ell (ldu), type by prec
     void* V;                  // m x (ell+1) (ldv)
     double* B;                // ell x ell, column-major
@@ -191,6 +192,12 @@ cudaError_t launch_rotate(cudaStream_t st, const T* in, int64_t ldin, int ell, c
 template <typename T>
 cudaError_t launch_sign_fix(cudaStream_t st, T* U, int64_t n, T* V, int64_t m, int k, int* signs);
 cudaError_t launch_small_svd(const Sv& sv, cudaStream_t st, int restart_ready);
+// tcgen05 block products (block_tc.cu): D base-16 digits per vector, q D <= 128
+bool block_tc_usable(const gkl_handle* h);
+bool block_tc_prepare(gkl_handle* h);
+size_t block_tc_scratch_bytes(const gkl_handle* h, int q);
+cudaError_t launch_block_product_tc(const gkl_handle* h, bool transpose, const float* X, int64_t ldx, int q, int D,
+                                    float* Y, int64_t ldy, void* scratch, int* nlaunch);
 // block form (block.cu)
 int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, float* Vout, double* resid,
               gkl_info* info);

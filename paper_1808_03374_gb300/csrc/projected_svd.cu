@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(1024) k_svd32(Sv sv) {
     float* W = fsm;
     float* Qm = W + ell * ell;
     __shared__ int s_rot;
+    __shared__ float s_maxr;  // largest |cos| of a rotated pair in the sweep
     __shared__ double s_sig[GKL_MAX_ELL];
     __shared__ int s_rank[GKL_MAX_ELL];
     for (int t = threadIdx.x; t < ell * ell; t += blockDim.x) {
@@ -100,60 +101,79 @@ __global__ void __launch_bounds__(1024) k_svd32(Sv sv) {
     const int N = ell + (ell & 1);
     const int npairs = N / 2;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    // one half-warp per pair (64 pairs in flight for ell = 128): 16 lanes x up to
+    // 8 rows each, 4 shuffle stages per dot product
+    const int hl = lane & 15, nhalf = 2 * nw;
     const float jtol = 2.f * sqrtf((float)ell) * 5.9604645e-08f;
     int sweep = 0;
+    float prev = 1.f;
     for (; sweep < 40; ++sweep) {
-        if (threadIdx.x == 0) s_rot = 0;
+        if (threadIdx.x == 0) {
+            s_rot = 0;
+            s_maxr = 0.f;
+        }
         __syncthreads();
         for (int rnd = 0; rnd < N - 1; ++rnd) {
-            for (int p = warp; p < npairs; p += nw) {
-                int a, b;
-                if (p == 0) {
-                    a = 0;
-                    b = 1 + rnd % (N - 1);
-                } else {
-                    a = 1 + (rnd + p) % (N - 1);
-                    b = 1 + (rnd + N - 1 - p) % (N - 1);
+            for (int p0 = 0; p0 < npairs; p0 += nhalf) {
+                const int p = p0 + 2 * warp + (lane >> 4);
+                int a = 0, b = 0;
+                bool act = p < npairs;
+                if (act) {
+                    if (p == 0) {
+                        a = 0;
+                        b = 1 + rnd % (N - 1);
+                    } else {
+                        a = 1 + (rnd + p) % (N - 1);
+                        b = 1 + (rnd + N - 1 - p) % (N - 1);
+                    }
+                    act = a < ell && b < ell;
                 }
-                if (a >= ell || b >= ell) continue;
                 float* wa = W + a * ell;
                 float* wb = W + b * ell;
                 float al = 0.f, be = 0.f, ga = 0.f;
-                for (int r = lane; r < ell; r += 32) {
-                    float x = wa[r], y = wb[r];
-                    al = fmaf(x, x, al);
-                    be = fmaf(y, y, be);
-                    ga = fmaf(x, y, ga);
-                }
+                if (act)
+                    for (int r = hl; r < ell; r += 16) {
+                        const float x = wa[r], y = wb[r];
+                        al = fmaf(x, x, al);
+                        be = fmaf(y, y, be);
+                        ga = fmaf(x, y, ga);
+                    }
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
+                for (int o = 8; o > 0; o >>= 1) {
                     al += __shfl_xor_sync(0xffffffffu, al, o);
                     be += __shfl_xor_sync(0xffffffffu, be, o);
                     ga += __shfl_xor_sync(0xffffffffu, ga, o);
                 }
-                if (ga == 0.f || fabsf(ga) <= jtol * sqrtf(al * be)) continue;
-                float zeta = (be - al) / (2.f * ga);
-                float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-                float cs = 1.f / sqrtf(1.f + t * t), sn = cs * t;
-                for (int r = lane; r < ell; r += 32) {
-                    float x = wa[r], y = wb[r];
+                if (!act || ga == 0.f || fabsf(ga) <= jtol * sqrtf(al * be)) continue;
+                if (hl == 0) atomicMax(reinterpret_cast<int*>(&s_maxr), __float_as_int(fabsf(ga) / sqrtf(al * be)));
+                const float zeta = (be - al) / (2.f * ga);
+                const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+                const float cs = 1.f / sqrtf(1.f + t * t), sn = cs * t;
+                for (int r = hl; r < ell; r += 16) {
+                    const float x = wa[r], y = wb[r];
                     wa[r] = cs * x - sn * y;
                     wb[r] = sn * x + cs * y;
                 }
                 float* qa = Qm + a * ell;
                 float* qb = Qm + b * ell;
-                for (int r = lane; r < ell; r += 32) {
-                    float x = qa[r], y = qb[r];
+                for (int r = hl; r < ell; r += 16) {
+                    const float x = qa[r], y = qb[r];
                     qa[r] = cs * x - sn * y;
                     qb[r] = sn * x + cs * y;
                 }
-                if (lane == 0) s_rot = 1;
+                if (hl == 0) s_rot = 1;
             }
             __syncthreads();
         }
         const int rot = s_rot;
+        const float maxr = s_maxr;
         __syncthreads();
         if (!rot) break;
+        // Near convergence Jacobi is quadratic: a sweep that does not halve the
+        // largest remaining |cos|, already within 16x the threshold, is at FP32
+        // rounding level (the FP64 refinement that follows takes it from there).
+        if (maxr < 16.f * jtol && maxr > 0.5f * prev) break;
+        prev = maxr;
     }
     for (int c = warp; c < ell; c += nw) {
         double s2 = 0.0;
@@ -437,6 +457,23 @@ __global__ void __launch_bounds__(512) k_svd64(Sv sv, int restart_ready, double*
     conv_and_restart(sv, restart_ready, 1000 + sweep);
 }
 
+// Where the refinement does not apply (clustered or tiny kept values), take the
+// FP32 Jacobi triplets as they are (sorted, in sv.rw): used by the block form,
+// whose bases are FP32, instead of the FP64 Jacobi.
+__global__ void __launch_bounds__(256) k_svd_take32(Sv sv, int restart_ready) {
+    if (sv.sc->abort || !sv.sc->svd_fallback) return;
+    const int ell = sv.ell;
+    const double* U0 = sv.rw;
+    const double* V0 = U0 + ell * ell;
+    const double* sig0 = sv.rw + 7 * ell * ell;
+    for (int t = threadIdx.x; t < ell * ell; t += blockDim.x) {
+        sv.P[t] = U0[t];
+        sv.Q[t] = V0[t];
+    }
+    for (int c = threadIdx.x; c < ell; c += blockDim.x) sv.co->sg[c] = sig0[c];
+    conv_and_restart(sv, restart_ready, sv.co->sweeps);
+}
+
 cudaError_t launch_small_svd(const Sv& sv, cudaStream_t st, int restart_ready) {
     const int ell = sv.ell;
     const size_t ell2 = (size_t)ell * ell;
@@ -459,6 +496,10 @@ cudaError_t launch_small_svd(const Sv& sv, cudaStream_t st, int restart_ready) {
     k_ref_b<<<ell, 128, 0, st>>>(sv, U0, V0, U1, V1);
     k_ref_a<<<ell, 128, 0, st>>>(sv, U1, V1);  // check of the result
     k_svd_final<<<1, 256, 0, st>>>(sv, U1, V1, restart_ready);
+    if (sv.fp32_only) {
+        k_svd_take32<<<1, 256, 0, st>>>(sv, restart_ready);
+        return cudaGetLastError();
+    }
     // FP64 fallback (returns at once unless requested above)
     size_t smem = 2 * ell2 * sizeof(double);
     double* scratch = nullptr;

@@ -26,7 +26,7 @@ _DTYPE = {FP64: torch.float64, FP32: torch.float32, BLOCK: torch.float32}
 
 EXPORTS = ["gkl_version", "gkl_last_error", "gkl_opts_default", "gkl_colstats", "gkl_init", "gkl_set_stream",
            "gkl_set_weights", "gkl_matvec", "gkl_rmatvec", "gkl_svd", "gkl_destroy", "gkl_matvec_noalloc",
-           "gkl_grad"]
+           "gkl_grad", "gkl_matmat"]
 
 
 class GKLError(RuntimeError):
@@ -82,6 +82,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.gkl_matvec_noalloc.argtypes = [vp, i64, i64, i64, vp, vp, i32, vp, vp, vp]
     lib.gkl_grad.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double]
     lib.gkl_grad.restype = ctypes.c_int
+    lib.gkl_matmat.argtypes = [vp, i32, i32, i32, vp, i64, vp, i64]
+    lib.gkl_matmat.restype = ctypes.c_int
     for f in ("gkl_colstats", "gkl_init", "gkl_set_stream", "gkl_set_weights", "gkl_matvec", "gkl_rmatvec",
               "gkl_svd", "gkl_destroy", "gkl_matvec_noalloc"):
         getattr(lib, f).restype = ctypes.c_int
@@ -192,6 +194,20 @@ class GKL:
         self._sync_stream()
         _check(lib().gkl_rmatvec(self._h, prec, _ptr(u), _ptr(x)), self._h)
         return x
+
+    def matmat(self, X: torch.Tensor, transpose: bool = False, digits: int = 8,
+               out: torch.Tensor | None = None) -> torch.Tensor:
+        """Block product on the tensor cores: A X (X m x q) or A^T X (X n x q),
+        q <= 32, FP32; `digits` 8 (finer than FP32) or 4 (16-bit fixed point).
+        X and the result are row-major q x rows tensors (column-major rows x q)."""
+        rows_in, rows_out = (self.n, self.m) if transpose else (self.m, self.n)
+        assert X.is_cuda and X.dtype == torch.float32 and X.dim() == 2 and X.shape[1] == rows_in
+        assert X.is_contiguous()
+        q = X.shape[0]
+        Y = out if out is not None else torch.empty((q, rows_out), dtype=torch.float32, device=self.device)
+        self._sync_stream()
+        _check(lib().gkl_matmat(self._h, int(transpose), q, digits, _ptr(X), rows_in, _ptr(Y), rows_out), self._h)
+        return Y
 
     def svd(self, k: int, ell: int, reorth: str = "full", precision: str = "fp64", tol: float = 1e-10,
             maxit: int = 1000, k_keep: int = 0, omega: float = 0.0, seed: int = 1,
