@@ -186,6 +186,29 @@ __global__ void k_block_random(float* __restrict__ X, int64_t ldx, int64_t len, 
 }
 
 
+// Restart projection of the kept Ritz pairs, in FP64: M = T Q[:, :kk] (ell x kk)
+// and Tn = P[:, :kk]^T M (kk x kk), so that A V Q_kk = (U P_kk) Tn up to the
+// coupling to the discarded pairs (small when P and Q are accurate Ritz
+// vectors); Tn is diagonal only when P and Q are exact.
+__global__ void __launch_bounds__(128) k_tq(const double* __restrict__ T, const double* __restrict__ Q, int ell,
+                                            int kk, double* __restrict__ M) {
+    const int j = blockIdx.x;
+    for (int r = threadIdx.x; r < ell; r += blockDim.x) {
+        double s = 0.0;
+        for (int c = 0; c < ell; ++c) s += T[r + (int64_t)c * ell] * Q[c + (int64_t)j * ell];
+        M[r + (int64_t)j * ell] = s;
+    }
+}
+__global__ void __launch_bounds__(128) k_ptm(const double* __restrict__ P, const double* __restrict__ M, int ell,
+                                             int kk, double* __restrict__ Tn) {
+    const int j = blockIdx.x;
+    for (int i = threadIdx.x; i < kk; i += blockDim.x) {
+        double s = 0.0;
+        for (int r = 0; r < ell; ++r) s += P[r + (int64_t)i * ell] * M[r + (int64_t)j * ell];
+        Tn[i + (int64_t)j * kk] = s;
+    }
+}
+
 // ---- batched block products (every code decoded once for all q vectors) -------
 
 // X[:, 0:q] = A^T U[:, 0:q] (q <= 32), FP32.  A block owns 128 SNPs and all q
@@ -831,13 +854,22 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
         if (e == cudaSuccess)
             e = cudaMemcpy2DAsync(V2 + (int64_t)kk * ldv, sizeof(float) * ldv, V + (int64_t)ell * ldv,
                                   sizeof(float) * ldv, sizeof(float) * m, b, cudaMemcpyDeviceToDevice, c.st);
+        // kept block of T: the FP64 projection P_kk^T T Q_kk (T is still in sv.B)
+        double* Mtq = sv.rw + 4 * ell2;  // refinement workspace, free after the SVD
+        double* Tn = sv.rw + 5 * ell2;
+        std::vector<double> hTn;
+        if (e == cudaSuccess) {
+            k_tq<<<kk, 128, 0, c.st>>>(sv.B, sv.Q, ell, kk, Mtq);
+            k_ptm<<<kk, 128, 0, c.st>>>(sv.P, Mtq, ell, kk, Tn);
+            e = download(c, Tn, hTn, (size_t)kk * kk);
+        }
         if (e != cudaSuccess) return fail("restart");
-        c.launches += 2;
+        c.launches += 4;
         std::swap(U, U2);
         std::swap(V, V2);
         std::fill(T.begin(), T.end(), 0.0);
         for (int i = 0; i < kk; ++i) {
-            T[i + (size_t)ell * i] = sg[i];
+            for (int j = 0; j < kk; ++j) T[i + (size_t)ell * j] = hTn[i + (size_t)kk * j];
             for (int cc = 0; cc < b; ++cc) T[i + (size_t)ell * (kk + cc)] = SP[cc + (size_t)b * i];
         }
         ++restarts;

@@ -80,95 +80,135 @@ __device__ void conv_and_restart(const Sv& sv, int restart_ready, int sweeps) {
 // ---------------------------------------------------------------- FP32 Jacobi
 
 // Round-robin parallel ordering: ell/2 disjoint column pairs per round, one
-// warp per pair.  Works on B rounded to FP32.  Writes the approximate sorted
-// triplets (U0 normalised left vectors, V0 right vectors, sig0) in FP64 and
-// decides whether refinement applies.
+// half-warp per pair (64 pairs in flight for ell = 128).  Works on B rounded to
+// FP32, columns padded with zero rows to LD = 16 RPL so that each lane holds
+// RPL consecutive rows (vector shared-memory accesses).  Column norms are kept
+// and updated by each rotation (alpha' = alpha - t gamma, beta' = beta + t
+// gamma), recomputed at every sweep, so a pair costs one dot product.  Writes
+// the approximate sorted triplets (U0 normalised left vectors, V0 right
+// vectors, sig0) in FP64 and decides whether refinement applies.
+template <int RPL>
+__device__ __forceinline__ void ld_rows(const float* p, float (&v)[RPL]) {
+#pragma unroll
+    for (int k = 0; k < RPL; k += 4) {
+        const float4 x = *reinterpret_cast<const float4*>(p + k);
+        v[k] = x.x;
+        v[k + 1] = x.y;
+        v[k + 2] = x.z;
+        v[k + 3] = x.w;
+    }
+}
+template <int RPL>
+__device__ __forceinline__ void st_rows(float* p, const float (&v)[RPL]) {
+#pragma unroll
+    for (int k = 0; k < RPL; k += 4) *reinterpret_cast<float4*>(p + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+}
+
+template <int RPL>
 __global__ void __launch_bounds__(1024) k_svd32(Sv sv) {
+    static_assert(RPL % 4 == 0, "rows per lane: whole float4");
     if (sv.sc->abort) return;
-    extern __shared__ float fsm[];
+    constexpr int LD = 16 * RPL;
+    extern __shared__ __align__(16) float fsm[];
     const int ell = sv.ell;
     float* W = fsm;
-    float* Qm = W + ell * ell;
-    __shared__ int s_rot;
-    __shared__ float s_maxr;  // largest |cos| of a rotated pair in the sweep
+    float* Qm = W + ell * LD;
+    __shared__ float s_nrm[GKL_MAX_ELL];
+    __shared__ float s_wmax[32];
     __shared__ double s_sig[GKL_MAX_ELL];
     __shared__ int s_rank[GKL_MAX_ELL];
-    for (int t = threadIdx.x; t < ell * ell; t += blockDim.x) {
-        W[t] = (float)sv.B[t];
-        Qm[t] = (t % ell == t / ell) ? 1.f : 0.f;
+    for (int t = threadIdx.x; t < ell * LD; t += blockDim.x) {
+        const int r = t % LD, c = t / LD;
+        W[t] = r < ell ? (float)sv.B[r + c * ell] : 0.f;
+        Qm[t] = r == c ? 1.f : 0.f;
     }
     __syncthreads();
     const int N = ell + (ell & 1);
     const int npairs = N / 2;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    // one half-warp per pair (64 pairs in flight for ell = 128): 16 lanes x up to
-    // 8 rows each, 4 shuffle stages per dot product
-    const int hl = lane & 15, nhalf = 2 * nw;
+    const int hl = lane & 15, r0 = RPL * hl;
+    const int p = 2 * warp + (lane >> 4);  // this half-warp's pair slot
     const float jtol = 2.f * sqrtf((float)ell) * 5.9604645e-08f;
     int sweep = 0;
     float prev = 1.f;
     for (; sweep < 40; ++sweep) {
-        if (threadIdx.x == 0) {
-            s_rot = 0;
-            s_maxr = 0.f;
+        // exact column norms at the start of each sweep
+        for (int c = warp; c < ell; c += nw) {
+            float s2 = 0.f;
+            for (int r = lane; r < LD; r += 32) s2 = fmaf(W[r + c * LD], W[r + c * LD], s2);
+            for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            if (lane == 0) s_nrm[c] = s2;
         }
         __syncthreads();
+        float mymax = 0.f;
         for (int rnd = 0; rnd < N - 1; ++rnd) {
-            for (int p0 = 0; p0 < npairs; p0 += nhalf) {
-                const int p = p0 + 2 * warp + (lane >> 4);
-                int a = 0, b = 0;
-                bool act = p < npairs;
-                if (act) {
-                    if (p == 0) {
-                        a = 0;
-                        b = 1 + rnd % (N - 1);
-                    } else {
-                        a = 1 + (rnd + p) % (N - 1);
-                        b = 1 + (rnd + N - 1 - p) % (N - 1);
-                    }
-                    act = a < ell && b < ell;
+            int a = 0, b = 0;
+            bool act = p < npairs;
+            if (act) {
+                // round-robin pairing without integer division: (rnd +- p) mod (N - 1)
+                if (p == 0) {
+                    a = 0;
+                    b = 1 + rnd;
+                } else {
+                    int x = rnd + p, y = rnd - p;
+                    if (x >= N - 1) x -= N - 1;
+                    if (y < 0) y += N - 1;
+                    a = 1 + x;
+                    b = 1 + y;
                 }
-                float* wa = W + a * ell;
-                float* wb = W + b * ell;
-                float al = 0.f, be = 0.f, ga = 0.f;
-                if (act)
-                    for (int r = hl; r < ell; r += 16) {
-                        const float x = wa[r], y = wb[r];
-                        al = fmaf(x, x, al);
-                        be = fmaf(y, y, be);
-                        ga = fmaf(x, y, ga);
-                    }
+                act = a < ell && b < ell;
+            }
+            float xa[RPL], xb[RPL];
+            float ga = 0.f;
+            if (act) {
+                ld_rows<RPL>(W + a * LD + r0, xa);
+                ld_rows<RPL>(W + b * LD + r0, xb);
 #pragma unroll
-                for (int o = 8; o > 0; o >>= 1) {
-                    al += __shfl_xor_sync(0xffffffffu, al, o);
-                    be += __shfl_xor_sync(0xffffffffu, be, o);
-                    ga += __shfl_xor_sync(0xffffffffu, ga, o);
+                for (int k = 0; k < RPL; ++k) ga = fmaf(xa[k], xb[k], ga);
+            }
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
+            if (act) {
+                const float al = s_nrm[a], be = s_nrm[b];
+                if (ga != 0.f && fabsf(ga) > jtol * sqrtf(al * be)) {
+                    mymax = fmaxf(mymax, fabsf(ga) / sqrtf(al * be));
+                    const float zeta = (be - al) / (2.f * ga);
+                    const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+                    const float cs = 1.f / sqrtf(1.f + t * t), sn = cs * t;
+#pragma unroll
+                    for (int k = 0; k < RPL; ++k) {
+                        const float x = xa[k], y = xb[k];
+                        xa[k] = cs * x - sn * y;
+                        xb[k] = sn * x + cs * y;
+                    }
+                    st_rows<RPL>(W + a * LD + r0, xa);
+                    st_rows<RPL>(W + b * LD + r0, xb);
+                    ld_rows<RPL>(Qm + a * LD + r0, xa);
+                    ld_rows<RPL>(Qm + b * LD + r0, xb);
+#pragma unroll
+                    for (int k = 0; k < RPL; ++k) {
+                        const float x = xa[k], y = xb[k];
+                        xa[k] = cs * x - sn * y;
+                        xb[k] = sn * x + cs * y;
+                    }
+                    st_rows<RPL>(Qm + a * LD + r0, xa);
+                    st_rows<RPL>(Qm + b * LD + r0, xb);
+                    if (hl == 0) {
+                        s_nrm[a] = al - t * ga;
+                        s_nrm[b] = be + t * ga;
+                    }
                 }
-                if (!act || ga == 0.f || fabsf(ga) <= jtol * sqrtf(al * be)) continue;
-                if (hl == 0) atomicMax(reinterpret_cast<int*>(&s_maxr), __float_as_int(fabsf(ga) / sqrtf(al * be)));
-                const float zeta = (be - al) / (2.f * ga);
-                const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-                const float cs = 1.f / sqrtf(1.f + t * t), sn = cs * t;
-                for (int r = hl; r < ell; r += 16) {
-                    const float x = wa[r], y = wb[r];
-                    wa[r] = cs * x - sn * y;
-                    wb[r] = sn * x + cs * y;
-                }
-                float* qa = Qm + a * ell;
-                float* qb = Qm + b * ell;
-                for (int r = hl; r < ell; r += 16) {
-                    const float x = qa[r], y = qb[r];
-                    qa[r] = cs * x - sn * y;
-                    qb[r] = sn * x + cs * y;
-                }
-                if (hl == 0) s_rot = 1;
             }
             __syncthreads();
         }
-        const int rot = s_rot;
-        const float maxr = s_maxr;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mymax = fmaxf(mymax, __shfl_xor_sync(0xffffffffu, mymax, o));
+        if (lane == 0) s_wmax[warp] = mymax;
         __syncthreads();
-        if (!rot) break;
+        float maxr = 0.f;
+        for (int w2 = 0; w2 < nw; ++w2) maxr = fmaxf(maxr, s_wmax[w2]);
+        __syncthreads();
+        if (maxr == 0.f) break;  // no rotation in the sweep
         // Near convergence Jacobi is quadratic: a sweep that does not halve the
         // largest remaining |cos|, already within 16x the threshold, is at FP32
         // rounding level (the FP64 refinement that follows takes it from there).
@@ -177,7 +217,7 @@ __global__ void __launch_bounds__(1024) k_svd32(Sv sv) {
     }
     for (int c = warp; c < ell; c += nw) {
         double s2 = 0.0;
-        for (int r = lane; r < ell; r += 32) s2 += (double)W[r + c * ell] * (double)W[r + c * ell];
+        for (int r = lane; r < ell; r += 32) s2 += (double)W[r + c * LD] * (double)W[r + c * LD];
         s2 = warp_sum(s2);
         if (lane == 0) s_sig[c] = sqrt(s2);
     }
@@ -196,8 +236,8 @@ __global__ void __launch_bounds__(1024) k_svd32(Sv sv) {
         int r = t % ell, c = t / ell;
         int dst = s_rank[c];
         double sg = s_sig[c];
-        U0[r + dst * ell] = sg > 0.0 ? (double)W[t] / sg : 0.0;
-        V0[r + dst * ell] = (double)Qm[t];
+        U0[r + dst * ell] = sg > 0.0 ? (double)W[r + c * LD] / sg : 0.0;
+        V0[r + dst * ell] = (double)Qm[r + c * LD];
     }
     for (int c = threadIdx.x; c < ell; c += blockDim.x) sig0[s_rank[c]] = s_sig[c];
     __syncthreads();
@@ -477,13 +517,15 @@ __global__ void __launch_bounds__(256) k_svd_take32(Sv sv, int restart_ready) {
 cudaError_t launch_small_svd(const Sv& sv, cudaStream_t st, int restart_ready) {
     const int ell = sv.ell;
     const size_t ell2 = (size_t)ell * ell;
-    // FP32 Jacobi
-    size_t smem32 = 2 * ell2 * sizeof(float);
+    // FP32 Jacobi: rows per lane 4 or 8 (columns padded to 64 or 128 rows)
+    const int rpl = ell <= 64 ? 4 : 8;
+    const size_t smem32 = 2 * (size_t)ell * 16 * rpl * sizeof(float);
+    auto kfn = rpl == 4 ? k_svd32<4> : k_svd32<8>;
     if (smem32 > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_svd32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32);
+        cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32);
         if (e != cudaSuccess) return e;
     }
-    k_svd32<<<1, 1024, smem32, st>>>(sv);
+    kfn<<<1, 1024, smem32, st>>>(sv);
     double* U0 = sv.rw;
     double* V0 = U0 + ell2;
     double* U1 = V0 + ell2;
