@@ -41,10 +41,12 @@ constexpr int kMaxB = 32;       // block size limit (Gram kernel tile)
 // ---- kernels ------------------------------------------------------------------
 
 // part[blk][i + p j] = sum over the block's rows r of X[r + i ldx] Y[r + j ldy]
-// (i < p <= 128, j < q <= 32): FP32 products summed over 32-row chunks, the
-// chunk sums added in FP64.  Each chunk is loaded into registers while the
-// previous one is multiplied out of shared memory (two buffers, one barrier
-// per chunk).
+// (i < p <= 128, j < q <= 8 QC):
+// FP32 products summed over 32-row chunks, the chunk sums added in FP64.  Each
+// chunk is loaded into registers while the previous one is multiplied out of
+// shared memory (two buffers, one barrier per chunk).  QC = 2 serves q <= 16
+// without idle threads, QC = 4 q <= 32.
+template <int QC>
 __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ X, int64_t ldx, int p,
                                                     const float* __restrict__ Y, int64_t ldy, int q, int64_t len,
                                                     int64_t rows_per_blk, double* __restrict__ part) {
@@ -54,12 +56,12 @@ __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ X, 
     const int lr = t & 31, lc = t >> 5;  // load role: row lr, columns lc + 8 k
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_blk;
     const int64_t r1 = min(len, r0 + rows_per_blk);
-    double acc[4][4];
+    double acc[4][QC];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[a][c] = 0.0;
-    float xr[16], yr[4];
+        for (int c = 0; c < QC; ++c) acc[a][c] = 0.0;
+    float xr[16], yr[QC];
     auto load = [&](int64_t rb) {
         const int64_t r = rb + lr;
         const bool ok = r < r1;
@@ -69,7 +71,7 @@ __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ X, 
             xr[k] = (ok && c < p) ? X[r + (int64_t)c * ldx] : 0.f;
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < QC; ++k) {
             const int c = lc + 8 * k;
             yr[k] = (ok && c < q) ? Y[r + (int64_t)c * ldy] : 0.f;
         }
@@ -80,69 +82,72 @@ __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ X, 
 #pragma unroll
         for (int k = 0; k < 16; ++k) sx[buf][lr][lc + 8 * k] = xr[k];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) sy[buf][lr][lc + 8 * k] = yr[k];
+        for (int k = 0; k < QC; ++k) sy[buf][lr][lc + 8 * k] = yr[k];
         __syncthreads();
         if (rb + kGramRows < r1) load(rb + kGramRows);
-        float f[4][4];
+        float f[4][QC];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) f[a][c] = 0.f;
+            for (int c = 0; c < QC; ++c) f[a][c] = 0.f;
 #pragma unroll 8
         for (int rr = 0; rr < kGramRows; ++rr) {
-            float xa[4], yc[4];
+            float xa[4], yc[QC];
 #pragma unroll
             for (int a = 0; a < 4; ++a) xa[a] = sx[buf][rr][gi + 32 * a];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) yc[c] = sy[buf][rr][gj + 8 * c];
+            for (int c = 0; c < QC; ++c) yc[c] = sy[buf][rr][gj + 8 * c];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) f[a][c] = fmaf(xa[a], yc[c], f[a][c]);
+                for (int c = 0; c < QC; ++c) f[a][c] = fmaf(xa[a], yc[c], f[a][c]);
         }
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[a][c] += (double)f[a][c];
+            for (int c = 0; c < QC; ++c) acc[a][c] += (double)f[a][c];
     }
     double* out = part + (int64_t)blockIdx.x * p * q;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < QC; ++c) {
             const int i = gi + 32 * a, j = gj + 8 * c;
             if (i < p && j < q) out[i + p * j] = acc[a][c];
         }
 }
 
-// out[e] = sum_blk part[blk][e] in block order (deterministic); eight loads in flight.
-__global__ void __launch_bounds__(64) k_gram_sum(const double* __restrict__ part, int nblk, int pq,
-                                                 double* __restrict__ out) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= pq) return;
+// out[e] = sum_blk part[blk][e] in a fixed order (deterministic): 32 elements
+// per block; warp w sums blocks w, w + 8, ... (coalesced rows of 32 doubles),
+// then the eight warp sums are added in warp order.
+__global__ void __launch_bounds__(256) k_gram_sum(const double* __restrict__ part, int nblk, int pq,
+                                                  double* __restrict__ out) {
+    __shared__ double ws[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + lane;
     double s = 0.0;
-    int b = 0;
-    for (; b + 8 <= nblk; b += 8) {
-        double v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = part[(int64_t)(b + u) * pq + e];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) s += v[u];
+    if (e < pq)
+        for (int b = w; b < nblk; b += 8) s += part[(int64_t)b * pq + e];
+    ws[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && e < pq) {
+        double t = 0.0;
+        for (int k = 0; k < 8; ++k) t += ws[k][lane];
+        out[e] = t;
     }
-    for (; b < nblk; ++b) s += part[(int64_t)b * pq + e];
-    out[e] = s;
 }
 
-// X[:, 0:q] <- alpha X[:, 0:q] + beta Y[:, 0:p] C  (C p x q, FP64, column-major), per row.
+// X[:, 0:q] <- alpha X[:, 0:q] + beta Y[:, 0:p] C  (C p x q, FP64, column-major with
+// leading dimension ldc), per row.
 // X and Y may be the same buffer only with alpha = 0 (X <- beta X C).  C is
 // held row by row in shared memory (FP32, 32 columns) and read as float4.
 __global__ void __launch_bounds__(256) k_block_axpy(float* X, int64_t ldx, int q, const float* Y,
-                                                     int64_t ldy, int p, const double* __restrict__ C, float alpha,
-                                                     float beta, int64_t len) {
+                                                     int64_t ldy, int p, const double* __restrict__ C, int ldc,
+                                                     float alpha, float beta, int64_t len) {
     __shared__ __align__(16) float sc[128 * kMaxB];
     for (int e = threadIdx.x; e < p * kMaxB; e += blockDim.x) {
         const int i = e / kMaxB, j = e % kMaxB;
-        sc[e] = j < q ? (float)C[i + p * j] : 0.f;
+        sc[e] = j < q ? (float)C[i + ldc * j] : 0.f;
     }
     __syncthreads();
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < len; r += (int64_t)gridDim.x * blockDim.x) {
@@ -474,6 +479,7 @@ struct BlockCtx {
     uint32_t draw;
     int launches;
     int deflations;
+    int cgs_second;    // orthonormalisations that needed a second Gram-Schmidt pass
     double ms_mv, ms_rmv;
     int64_t products;
 };
@@ -488,8 +494,11 @@ static cudaError_t gram(BlockCtx& c, const float* X, int64_t ldx, int p, const f
                         int64_t len, double* C) {
     const int nb = gram_blocks(c, len);
     const int64_t rpb = (len + nb - 1) / nb;
-    k_gram_part<<<nb, 256, 0, c.st>>>(X, ldx, p, Y, ldy, q, len, rpb, c.d_part);
-    k_gram_sum<<<(p * q + 63) / 64, 64, 0, c.st>>>(c.d_part, nb, p * q, C);
+    if (q <= 16)
+        k_gram_part<2><<<nb, 256, 0, c.st>>>(X, ldx, p, Y, ldy, q, len, rpb, c.d_part);
+    else
+        k_gram_part<4><<<nb, 256, 0, c.st>>>(X, ldx, p, Y, ldy, q, len, rpb, c.d_part);
+    k_gram_sum<<<(p * q + 31) / 32, 256, 0, c.st>>>(c.d_part, nb, p * q, C);
     c.launches += 2;
     return cudaGetLastError();
 }
@@ -498,19 +507,27 @@ static int axpy_grid(const BlockCtx& c, int64_t len) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(4 * c.h->num_sms, (len + 255) / 256));
 }
 
-// X <- X - B (B^T X) twice, B = len x nb basis
+// One classical Gram-Schmidt pass X <- X - B (B^T X), B = len x nbasis; the
+// coefficients are left in C (nbasis x q).
+static cudaError_t cgs_pass(BlockCtx& c, float* X, int64_t ldx, int q, const float* B, int64_t ldb, int nbasis,
+                            int64_t len, double* C) {
+    cudaError_t e = gram(c, B, ldb, nbasis, X, ldx, q, len, C);
+    if (e != cudaSuccess) return e;
+    k_block_axpy<<<axpy_grid(c, len), 256, 0, c.st>>>(X, ldx, q, B, ldb, nbasis, C, nbasis, 1.f, -1.f, len);
+    c.launches += 1;
+    return cudaGetLastError();
+}
+
+// X <- X - B (B^T X) twice
 static cudaError_t cgs2(BlockCtx& c, float* X, int64_t ldx, int q, const float* B, int64_t ldb, int nbasis,
                         int64_t len) {
     if (nbasis == 0) return cudaSuccess;
     for (int pass = 0; pass < 2; ++pass) {
-        cudaError_t e = gram(c, B, ldb, nbasis, X, ldx, q, len, c.d_small);
+        cudaError_t e = cgs_pass(c, X, ldx, q, B, ldb, nbasis, len, c.d_small);
         if (e != cudaSuccess) return e;
-        k_block_axpy<<<axpy_grid(c, len), 256, 0, c.st>>>(X, ldx, q, B, ldb, nbasis, c.d_small, 1.f, -1.f, len);
-        c.launches += 1;
     }
-    return cudaGetLastError();
+    return cudaSuccess;
 }
-
 
 static cudaError_t upload(BlockCtx& c, const std::vector<double>& hm, double* dst) {
     return cudaMemcpyAsync(dst, hm.data(), sizeof(double) * hm.size(), cudaMemcpyHostToDevice, c.st);
@@ -551,11 +568,34 @@ static cudaError_t orthonormalize(BlockCtx& c, float* X, int64_t ldx, int q, con
 static cudaError_t orthonormalize_once(BlockCtx& c, float* X, int64_t ldx, int q, const float* B, int64_t ldb,
                                        int nb, int64_t len, std::vector<double>& R, bool& chol_ok) {
     chol_ok = false;
-    cudaError_t e = cgs2(c, X, ldx, q, B, ldb, nb, len);
-    std::vector<double> G, lam, Z;
-    if (e == cudaSuccess) e = gram(c, X, ldx, q, X, ldx, q, len, c.d_small);
-    if (e == cudaSuccess) e = download(c, c.d_small, G, (size_t)q * q);
+    // Gram-Schmidt against B, a second pass only where the first removed more
+    // than half of a column's squared norm (the Daniel-Gragg-Kaufman-Stewart
+    // criterion; with B orthonormal, ||x||^2 = ||x'||^2 + ||c||^2 for the
+    // coefficients c of the first pass); then G = X^T X
+    std::vector<double> G, lam, Z, Cf;
+    double* Gd = c.d_small + GKL_MAX_ELL * kMaxB;
+    cudaError_t e = cudaSuccess;
+    if (nb > 0) e = cgs_pass(c, X, ldx, q, B, ldb, nb, len, c.d_small);
+    if (e == cudaSuccess) e = gram(c, X, ldx, q, X, ldx, q, len, Gd);
+    if (e == cudaSuccess && nb > 0) {
+        Cf.resize((size_t)nb * q);
+        e = cudaMemcpyAsync(Cf.data(), c.d_small, sizeof(double) * nb * q, cudaMemcpyDeviceToHost, c.st);
+    }
+    if (e == cudaSuccess) e = download(c, Gd, G, (size_t)q * q);
     if (e != cudaSuccess) return e;
+    bool again = false;
+    for (int j = 0; j < q && nb > 0; ++j) {
+        double cc = 0.0;
+        for (int i = 0; i < nb; ++i) cc += Cf[i + (size_t)nb * j] * Cf[i + (size_t)nb * j];
+        if (!(cc <= G[j + (size_t)q * j])) again = true;
+    }
+    if (again) {
+        ++c.cgs_second;
+        e = cgs_pass(c, X, ldx, q, B, ldb, nb, len, c.d_small);
+        if (e == cudaSuccess) e = gram(c, X, ldx, q, X, ldx, q, len, Gd);
+        if (e == cudaSuccess) e = download(c, Gd, G, (size_t)q * q);
+        if (e != cudaSuccess) return e;
+    }
     sym_eig(q, G, lam, Z);
     // descending eigenvalues, so that replaced directions come last
     std::vector<int> ord(q);
@@ -578,7 +618,7 @@ static cudaError_t orthonormalize_once(BlockCtx& c, float* X, int64_t ldx, int q
     }
     e = upload(c, M, c.d_small);
     if (e != cudaSuccess) return e;
-    k_block_axpy<<<axpy_grid(c, len), 256, 0, c.st>>>(X, ldx, q, X, ldx, q, c.d_small, 0.f, 1.f, len);
+    k_block_axpy<<<axpy_grid(c, len), 256, 0, c.st>>>(X, ldx, q, X, ldx, q, c.d_small, q, 0.f, 1.f, len);
     c.launches += 1;
     if (repl) {
         k_block_random<<<axpy_grid(c, len), 256, 0, c.st>>>(X, ldx, len, repl, c.seed, c.draw);
@@ -598,7 +638,7 @@ static cudaError_t orthonormalize_once(BlockCtx& c, float* X, int64_t ldx, int q
     }
     const std::vector<double> R2i = inv_upper(q, R2);
     if ((e = upload(c, R2i, c.d_small)) != cudaSuccess) return e;
-    k_block_axpy<<<axpy_grid(c, len), 256, 0, c.st>>>(X, ldx, q, X, ldx, q, c.d_small, 0.f, 1.f, len);
+    k_block_axpy<<<axpy_grid(c, len), 256, 0, c.st>>>(X, ldx, q, X, ldx, q, c.d_small, q, 0.f, 1.f, len);
     c.launches += 1;
     R = matmul(q, R2, R1);
     chol_ok = true;
@@ -686,7 +726,7 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
                  oQ = take(sizeof(double) * ell2), oRw = take(sizeof(double) * 8 * ell2);
     const size_t oSc = take(sizeof(DevScal)), oCo = take(sizeof(CycleOut));
     const size_t oPart = take(sizeof(double) * (size_t)nblk * GKL_MAX_ELL * kMaxB),
-                 oSmall = take(sizeof(double) * GKL_MAX_ELL * kMaxB), oSigns = take(sizeof(int) * GKL_MAX_ELL);
+                 oSmall = take(sizeof(double) * 2 * GKL_MAX_ELL * kMaxB), oSigns = take(sizeof(int) * GKL_MAX_ELL);
     const size_t oOutU = take(sizeof(float) * n * k), oOutV = take(sizeof(float) * m * k);
     // products: tcgen05 with 8 digits per vector (finer than FP32) where the
     // handle supports it (GKL_BLOCK_PRODUCTS=simt selects the SIMT kernels)
@@ -735,6 +775,7 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
                0x42000000u,
                0,
                0,
+               0,
                0.0,
                0.0,
                0};
@@ -776,7 +817,7 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
                 for (int cc = 0; cc < b; ++cc)
                     for (int r = 0; r < j0; ++r) Cs[r + (size_t)j0 * cc] = T[r + (size_t)ell * (j0 + cc)];
                 if ((e = upload(c, Cs, c.d_small)) != cudaSuccess) return fail("coupling upload");
-                k_block_axpy<<<axpy_grid(c, n), 256, 0, c.st>>>(Wb, ldu, b, U, ldu, j0, c.d_small, 1.f, -1.f, n);
+                k_block_axpy<<<axpy_grid(c, n), 256, 0, c.st>>>(Wb, ldu, b, U, ldu, j0, c.d_small, j0, 1.f, -1.f, n);
                 c.launches += 1;
             }
             if ((e = orthonormalize(c, Wb, ldu, b, U, ldu, j0, n, R)) != cudaSuccess) return fail("U block");
@@ -790,7 +831,7 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
                     for (int jj = 0; jj < b; ++jj) Rt[i + (size_t)b * jj] = R[jj + (size_t)b * i];
                 if ((e = upload(c, Rt, c.d_small)) != cudaSuccess) return fail("R upload");
                 k_block_axpy<<<axpy_grid(c, m), 256, 0, c.st>>>(Zb, ldv, b, V + (int64_t)j0 * ldv, ldv, b,
-                                                               c.d_small, 1.f, -1.f, m);
+                                                               c.d_small, b, 1.f, -1.f, m);
                 c.launches += 1;
             }
             if ((e = orthonormalize(c, Zb, ldv, b, V, ldv, j0 + b, m, S)) != cudaSuccess) return fail("V block");
@@ -907,19 +948,19 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
         }
         e = upload(c, Cv, c.d_small);
         if (e == cudaSuccess) {
-            k_block_axpy<<<axpy_grid(c, m), 256, 0, c.st>>>(Vo, m, k, Vk, ldv, k, c.d_small, 0.f, 1.f, m);
+            k_block_axpy<<<axpy_grid(c, m), 256, 0, c.st>>>(Vo, m, k, Vk, ldv, k, c.d_small, k, 0.f, 1.f, m);
             e = cudaStreamSynchronize(c.st);  // d_small is reused below
         }
         if (e == cudaSuccess) e = upload(c, Cu, c.d_small);
         if (e == cudaSuccess) {
-            k_block_axpy<<<axpy_grid(c, n), 256, 0, c.st>>>(Uo, n, k, Wk, ldu, k, c.d_small, 0.f, 1.f, n);
+            k_block_axpy<<<axpy_grid(c, n), 256, 0, c.st>>>(Uo, n, k, Wk, ldu, k, c.d_small, k, 0.f, 1.f, n);
             e = cudaStreamSynchronize(c.st);
         }
         // true residuals: Z = A^T U - V diag(sigma), r_i = ||Z_i||
         if (e == cudaSuccess) e = block_product(c, true, Uo, n, Vk, ldv, k);
         if (e == cudaSuccess) e = upload(c, Cs, c.d_small);
         if (e == cudaSuccess) {
-            k_block_axpy<<<axpy_grid(c, m), 256, 0, c.st>>>(Vk, ldv, k, Vo, m, k, c.d_small, 1.f, -1.f, m);
+            k_block_axpy<<<axpy_grid(c, m), 256, 0, c.st>>>(Vk, ldv, k, Vo, m, k, c.d_small, k, 1.f, -1.f, m);
             e = cudaStreamSynchronize(c.st);
         }
         if (e == cudaSuccess) e = gram(c, Vk, ldv, k, Vk, ldv, k, m, c.d_small);
@@ -969,6 +1010,7 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
         info->restarts = restarts;
         info->cycles = cycle + 1;
         info->breakdowns = c.deflations;
+        info->reorth_v = c.cgs_second;  // block form: orthonormalisations that needed a second CGS pass
         info->converged = converged;
         info->max_rel_resid = maxrel;
         info->dtheta1 = dtheta;

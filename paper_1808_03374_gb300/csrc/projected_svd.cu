@@ -82,16 +82,19 @@ __device__ void conv_and_restart(const Sv& sv, int restart_ready, int sweeps) {
 // Round-robin parallel ordering: ell/2 disjoint column pairs per round, one
 // half-warp per pair (64 pairs in flight for ell = 128).  Works on B rounded to
 // FP32, columns padded with zero rows to LD = 16 RPL so that each lane holds
-// RPL consecutive rows (vector shared-memory accesses).  Column norms are kept
+// RPL rows in float4 groups (vector shared-memory accesses).  Column norms are kept
 // and updated by each rotation (alpha' = alpha - t gamma, beta' = beta + t
 // gamma), recomputed at every sweep, so a pair costs one dot product.  Writes
 // the approximate sorted triplets (U0 normalised left vectors, V0 right
 // vectors, sig0) in FP64 and decides whether refinement applies.
+// Rows of lane hl: groups of four, 4 hl + 64 g + i (g < RPL / 4), so that the 16
+// lanes of a half-warp read 256 contiguous bytes per float4 access (no bank
+// conflicts between lanes).
 template <int RPL>
-__device__ __forceinline__ void ld_rows(const float* p, float (&v)[RPL]) {
+__device__ __forceinline__ void ld_rows(const float* col, int hl, float (&v)[RPL]) {
 #pragma unroll
     for (int k = 0; k < RPL; k += 4) {
-        const float4 x = *reinterpret_cast<const float4*>(p + k);
+        const float4 x = *reinterpret_cast<const float4*>(col + 16 * k + 4 * hl);
         v[k] = x.x;
         v[k + 1] = x.y;
         v[k + 2] = x.z;
@@ -99,9 +102,10 @@ __device__ __forceinline__ void ld_rows(const float* p, float (&v)[RPL]) {
     }
 }
 template <int RPL>
-__device__ __forceinline__ void st_rows(float* p, const float (&v)[RPL]) {
+__device__ __forceinline__ void st_rows(float* col, int hl, const float (&v)[RPL]) {
 #pragma unroll
-    for (int k = 0; k < RPL; k += 4) *reinterpret_cast<float4*>(p + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+    for (int k = 0; k < RPL; k += 4)
+        *reinterpret_cast<float4*>(col + 16 * k + 4 * hl) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
 }
 
 template <int RPL>
@@ -126,7 +130,7 @@ __global__ void __launch_bounds__(1024) k_svd32(Sv sv) {
     const int N = ell + (ell & 1);
     const int npairs = N / 2;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const int hl = lane & 15, r0 = RPL * hl;
+    const int hl = lane & 15;
     const int p = 2 * warp + (lane >> 4);  // this half-warp's pair slot
     const float jtol = 2.f * sqrtf((float)ell) * 5.9604645e-08f;
     int sweep = 0;
@@ -161,8 +165,8 @@ __global__ void __launch_bounds__(1024) k_svd32(Sv sv) {
             float xa[RPL], xb[RPL];
             float ga = 0.f;
             if (act) {
-                ld_rows<RPL>(W + a * LD + r0, xa);
-                ld_rows<RPL>(W + b * LD + r0, xb);
+                ld_rows<RPL>(W + a * LD, hl, xa);
+                ld_rows<RPL>(W + b * LD, hl, xb);
 #pragma unroll
                 for (int k = 0; k < RPL; ++k) ga = fmaf(xa[k], xb[k], ga);
             }
@@ -181,18 +185,18 @@ __global__ void __launch_bounds__(1024) k_svd32(Sv sv) {
                         xa[k] = cs * x - sn * y;
                         xb[k] = sn * x + cs * y;
                     }
-                    st_rows<RPL>(W + a * LD + r0, xa);
-                    st_rows<RPL>(W + b * LD + r0, xb);
-                    ld_rows<RPL>(Qm + a * LD + r0, xa);
-                    ld_rows<RPL>(Qm + b * LD + r0, xb);
+                    st_rows<RPL>(W + a * LD, hl, xa);
+                    st_rows<RPL>(W + b * LD, hl, xb);
+                    ld_rows<RPL>(Qm + a * LD, hl, xa);
+                    ld_rows<RPL>(Qm + b * LD, hl, xb);
 #pragma unroll
                     for (int k = 0; k < RPL; ++k) {
                         const float x = xa[k], y = xb[k];
                         xa[k] = cs * x - sn * y;
                         xb[k] = sn * x + cs * y;
                     }
-                    st_rows<RPL>(Qm + a * LD + r0, xa);
-                    st_rows<RPL>(Qm + b * LD + r0, xb);
+                    st_rows<RPL>(Qm + a * LD, hl, xa);
+                    st_rows<RPL>(Qm + b * LD, hl, xb);
                     if (hl == 0) {
                         s_nrm[a] = al - t * ga;
                         s_nrm[b] = be + t * ga;
