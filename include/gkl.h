@@ -57,8 +57,14 @@ typedef struct gkl_handle gkl_handle;
 #define GKL_FP32 1
 /* block form (Golub-Luk-Overton block bidiagonalisation; section 5 names block
  * methods as future work): blocks of gkl_opts.block vectors, FP32 bases, FP64
- * projected matrix; full block reorthogonalisation (reorth is ignored). */
+ * projected matrix, full block reorthogonalisation (reorth is ignored), block
+ * products on the tensor cores with each vector in 8 base-16 digits (finer
+ * than FP32), and a final Rayleigh-Ritz step. */
 #define GKL_BLOCK 2
+/* the same with 4-digit (16-bit fixed point, the precision of a split hi+lo
+ * BF16 pair) products during the iteration, 32 vectors per tensor-core pass;
+ * the final Rayleigh-Ritz step and the residuals use 8 digits. */
+#define GKL_BLOCK16 3
 
 /* reorthogonalisation strategy (section 3) */
 #define GKL_REORTH_FULL 0    /* CGS2 against all previous vectors at every step */
@@ -69,7 +75,7 @@ typedef struct gkl_opts {
     int32_t ell;        /* Krylov subspace size (restart length), k < ell <= min(n, m, 128) */
     int32_t k_keep;     /* Ritz vectors kept at a thick restart; 0 = k + (ell-k)/2 */
     int32_t reorth;     /* GKL_REORTH_FULL or GKL_REORTH_PARTIAL */
-    int32_t precision;  /* GKL_FP64, GKL_FP32 or GKL_BLOCK */
+    int32_t precision;  /* GKL_FP64, GKL_FP32, GKL_BLOCK or GKL_BLOCK16 */
     int32_t maxit;      /* maximum restart cycles (>= 1) */
     int32_t profile;    /* nonzero: time the packed-product kernels with CUDA events (gkl_info.ms_*) */
     int32_t block;      /* GKL_BLOCK: vectors per block, 1..32 (0 = 32); ell is rounded down to a
@@ -201,9 +207,14 @@ int gkl_matvec_noalloc(const uint8_t* packed, int64_t n, int64_t m, int64_t stri
  * Synchronises the stream.  Returns GKL_OK, GKL_NOT_CONVERGED (outputs hold
  * the last Ritz triplets), GKL_ERR_NONFINITE, GKL_ERR_ARG or GKL_ERR_CUDA.
  * The triplets of the FP64 / FP32 solvers stay in the handle for gkl_grad.
- * GKL_BLOCK: U and V are float; resid holds the block residuals
- * ||S_{s+1} P[last b rows, i]||; info->matvec_pairs counts vector pairs and
- * info->breakdowns the directions replaced by random vectors. */
+ * GKL_BLOCK / GKL_BLOCK16: U and V are float; for k <= 32 sigma, U, V come
+ * from the final Rayleigh-Ritz step and resid holds the true residuals
+ * ||A^T u_i - sigma_i v_i|| (8-digit products), otherwise the Ritz values and
+ * the block residuals ||S_{s+1} P[last b rows, i]||; the convergence test uses
+ * the block residuals; info->matvec_pairs counts vector pairs,
+ * info->breakdowns the directions replaced by random vectors and
+ * info->reorth_v the orthonormalisations that needed a second Gram-Schmidt
+ * pass. */
 int gkl_svd(gkl_handle* h, const gkl_opts* o, double* sigma, void* U, void* V,
             double* resid, gkl_info* info);
 

@@ -647,7 +647,8 @@ int gkl_svd(gkl_handle* h, const gkl_opts* o, double* sigma, void* U, void* V, d
     if (o->precision == GKL_FP64)
         return run_svd<double>(h, o, sigma, (double*)U, (double*)V, resid, info);
     if (o->precision == GKL_FP32) return run_svd<float>(h, o, sigma, (float*)U, (float*)V, resid, info);
-    if (o->precision == GKL_BLOCK) return run_block(h, o, sigma, (float*)U, (float*)V, resid, info);
+    if (o->precision == GKL_BLOCK || o->precision == GKL_BLOCK16)
+        return run_block(h, o, sigma, (float*)U, (float*)V, resid, info);
     return set_err(h, GKL_ERR_ARG, "unknown precision %d", o->precision);
 }
 

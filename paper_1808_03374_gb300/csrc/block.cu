@@ -728,15 +728,16 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
     const size_t oPart = take(sizeof(double) * (size_t)nblk * GKL_MAX_ELL * kMaxB),
                  oSmall = take(sizeof(double) * 2 * GKL_MAX_ELL * kMaxB), oSigns = take(sizeof(int) * GKL_MAX_ELL);
     const size_t oOutU = take(sizeof(float) * n * k), oOutV = take(sizeof(float) * m * k);
-    // products: tcgen05 with 8 digits per vector (finer than FP32) where the
-    // handle supports it (GKL_BLOCK_PRODUCTS=simt selects the SIMT kernels)
+    // products: tcgen05 with 8 digits per vector (finer than FP32), or 4 digits
+    // (GKL_BLOCK16) during the iteration, where the handle supports them
+    // (GKL_BLOCK_PRODUCTS=simt selects the SIMT kernels)
     const char* bpk = getenv("GKL_BLOCK_PRODUCTS");
     const bool use_tc = !(bpk && strcmp(bpk, "simt") == 0) && block_tc_prepare(h);
-    const int tc_digits = 8;
+    const int tc_digits = o->precision == GKL_BLOCK16 ? 4 : 8;
     int mvt, mvc;
     int64_t mvr, mvl;
     mv_chunks(h, b, mvt, mvc, mvr, mvl);
-    const size_t oBpart = use_tc ? take(block_tc_scratch_bytes(h, 128 / tc_digits))
+    const size_t oBpart = use_tc ? take(block_tc_scratch_bytes(h, kMaxB))
                                  : take(sizeof(float) * (size_t)mvc * (size_t)b * (size_t)mvl);
     void* ws = nullptr;
     if (cudaMalloc(&ws, off) != cudaSuccess) return set_err(h, GKL_ERR_CUDA, "block workspace of %zu bytes", off);
@@ -922,6 +923,7 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
     // and the true residuals ||A^T u_i - sigma_i v_i|| from one more product
     float* Uo = reinterpret_cast<float*>(W + oOutU);
     float* Vo = reinterpret_cast<float*>(W + oOutV);
+    c.tc_digits = 8;  // the Rayleigh-Ritz step and the residuals at full precision
     if (k <= kMaxB) {
         float* Vk = V2;  // m x k (ldv)
         float* Wk = U2;  // n x k (ldu)

@@ -16,13 +16,13 @@ import torch
 
 from .build import LIB as _LIB_PATH
 
-FP64, FP32, BLOCK = 0, 1, 2
+FP64, FP32, BLOCK, BLOCK16 = 0, 1, 2, 3
 REORTH_FULL, REORTH_PARTIAL = 0, 1
 OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, NOT_CONVERGED, ERR_GAP, ERR_STATE = range(7)
 
-_PREC = {"fp64": FP64, "fp32": FP32, "block": BLOCK}
+_PREC = {"fp64": FP64, "fp32": FP32, "block": BLOCK, "block16": BLOCK16}
 _REORTH = {"full": REORTH_FULL, "partial": REORTH_PARTIAL}
-_DTYPE = {FP64: torch.float64, FP32: torch.float32, BLOCK: torch.float32}
+_DTYPE = {FP64: torch.float64, FP32: torch.float32, BLOCK: torch.float32, BLOCK16: torch.float32}
 
 EXPORTS = ["gkl_version", "gkl_last_error", "gkl_opts_default", "gkl_colstats", "gkl_init", "gkl_set_stream",
            "gkl_set_weights", "gkl_matvec", "gkl_rmatvec", "gkl_svd", "gkl_destroy", "gkl_matvec_noalloc",

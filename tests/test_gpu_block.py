@@ -112,3 +112,16 @@ def test_block_simt_products_and_large_k(gk):
     assert r.converged
     rel = np.abs(r.sigma - ref.sigma[:40]) / ref.sigma[0]
     assert rel.max() < 1e-5, rel.max()
+
+
+def test_block16_split_precision_refined(gk):
+    """GKL_BLOCK16: the iteration runs on 16-bit fixed-point products (32
+    vectors per tensor-core pass); the final Rayleigh-Ritz step with 8-digit
+    products brings the singular values to 1e-6 of the FP64 oracle."""
+    g = small_geno(1503, 9_001, pops=5, miss=0.02, seed=61)
+    M = oracle_matrix(g)
+    k = 10
+    ref = oracle.gkl(M, k=k + 2, ell=40, tol=1e-13, v0=synth.normal_vec(4, 0, g.m), maxit=2000)
+    h = gk.GKL(to_dev(g.packed), g.n)
+    r = h.svd(k=k, ell=128, precision="block16", block=32, tol=1e-5, maxit=200, seed=9)
+    check(M, ref, r, k)
