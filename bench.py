@@ -48,6 +48,17 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def measured_e4m3_peak():
+    """Dense e4m3 tensor peak (TFLOP/s): the measured bf16 burst peak x 2 (the
+    nominal fp8/bf16 ratio), else the fallback 1.9 PFLOP/s bf16 x 2."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return 2.0 * float(d["bf16_tflops"]), "measured bf16 burst x 2"
+    return 3800.0, "fallback bf16 x 2"
+
+
 def source_digest(fn: str) -> str:
     """sha256 (16 hex) of one kernel source file under csrc/."""
     with open(os.path.join(ROOT, "paper_1808_03374_gb300", "csrc", fn), "rb") as f:
@@ -306,11 +317,35 @@ def run_ours(args):
         b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         nb = 3
         b0.record(stream)
+        binfos = []
         for _ in range(nb):
-            rb_ = h.svd(**bkw)
+            rb_ = h.svd(profile=True, **bkw)
+            binfos.append(rb_.info)
         b1.record(stream)
         torch.cuda.synchronize()
         bms = b0.elapsed_time(b1) / nb
+        # tensor roofline of the block products: per launch 16 ceil(m/128) ceil(stride/128)
+        # MMAs of M=128, N=256, K=32 (e4m3); algorithmic FLOP 2 n m q with q = 16 vectors
+        stride = (g.n + 3) // 4
+        stride = (stride + 15) // 16 * 16
+        mmas = 16 * ((g.m + 127) // 128) * ((stride + 127) // 128)
+        issued = 2.0 * 128 * 256 * 32 * mmas
+        algo = 2.0 * g.n * g.m * 16
+        tpeak, tsrc = measured_e4m3_peak()
+        bt = {}
+        for key, kn in (("rmv", "k_bt_rmv"), ("mv", "k_bt_mv")):
+            nl = sum(i["n_" + key] for i in binfos)
+            kms = sum(i["ms_" + key] for i in binfos) / max(1, nl)
+            bt[kn] = {"avg_launch_ms": kms, "launches": nl,
+                      "achieved_issued_tflops": issued / (kms / 1e3) / 1e12 if kms > 0 else None,
+                      "achieved_algorithmic_tflops": algo / (kms / 1e3) / 1e12 if kms > 0 else None,
+                      "traffic": ncu_traffic(kn, WORKLOAD)}
+        dom_bt = max(bt, key=lambda x: bt[x]["avg_launch_ms"] * bt[x]["launches"])
+        a_ = bt[dom_bt]["achieved_issued_tflops"]
+        block_roofline = {"bound": "tensor", "kernel": dom_bt, "achieved": a_, "peak": tpeak, "unit": "TFLOP/s",
+                          "frac": a_ / tpeak if a_ else None, "peak_source": tsrc,
+                          "traffic": bt[dom_bt]["traffic"], "issued_flop_per_launch": issued,
+                          "algorithmic_flop_per_launch": algo, "kernels": bt}
         # the FP32 single-vector solve with full reorthogonalisation: orthonormal
         # bases, so its true residual follows its reported one
         fkw = dict(solve_kw, reorth="full")
@@ -332,7 +367,8 @@ def run_ours(args):
                       "fp32_full_reorth": {"time_to_topk_ms": fms, "vector_pairs": rf.info["matvec_pairs"],
                                            "true_max_rel_resid": true_resid(rf),
                                            "reported_max_rel_resid": rf.info["max_rel_resid"]},
-                      "sigma_max_rel_diff_vs_fp32": float(np.max(np.abs(rb_.sigma - r.sigma)) / r.sigma[0])}
+                      "sigma_max_rel_diff_vs_fp32": float(np.max(np.abs(rb_.sigma - r.sigma)) / r.sigma[0]),
+                      "roofline": block_roofline}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

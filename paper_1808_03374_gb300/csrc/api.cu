@@ -367,7 +367,7 @@ static int run_svd(gkl_handle* h, const gkl_opts* o, double* sigma, T* Uout, T* 
             if (side == 0) side = 1;
             else { side = 0; ++j; }
         }
-        D.launches += 10;  // FP32 Jacobi, 3 x 2 refinement kernels, check, final, FP64 fallback
+        D.launches += 12;  // FP32 Jacobi, 4 x 2 refinement kernels, check, final, FP64 fallback
         D.mark(D.ev_svd, D.used_svd, false);
         if ((st = D.check(launch_small_svd(sv, h->stream, 1), "projected SVD"))) return st;
         D.mark(D.ev_svd, D.used_svd, true);

@@ -482,7 +482,37 @@ struct BlockCtx {
     int cgs_second;    // orthonormalisations that needed a second Gram-Schmidt pass
     double ms_mv, ms_rmv;
     int64_t products;
+    // profile: CUDA events around each main tensor-core kernel (pairs), kept
+    // until the solve's final synchronisation
+    bool profile = false;
+    bool cgs2_always = false;  // GKL_BLOCK_CGS=2: always two Gram-Schmidt passes
+    std::vector<cudaEvent_t> ev_mv, ev_rmv;
+    cudaEvent_t next_event(std::vector<cudaEvent_t>& pool, size_t& used) {
+        if (used == pool.size()) {
+            cudaEvent_t ev = nullptr;
+            cudaEventCreate(&ev);
+            pool.push_back(ev);
+        }
+        return pool[used++];
+    }
+    size_t used_mv = 0, used_rmv = 0;
+    ~BlockCtx() {
+        for (auto* pool : {&ev_mv, &ev_rmv})
+            for (cudaEvent_t ev : *pool)
+                if (ev) cudaEventDestroy(ev);
+    }
 };
+
+// Summed elapsed time of the recorded (begin, end) pairs; n = number of pairs.
+static double sum_event_pairs(const std::vector<cudaEvent_t>& pool, size_t used, int64_t* n) {
+    double ms = 0.0;
+    for (size_t i = 0; i + 1 < used; i += 2) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, pool[i], pool[i + 1]) == cudaSuccess) ms += t;
+    }
+    *n = (int64_t)(used / 2);
+    return ms;
+}
 
 static int gram_blocks(const BlockCtx& c, int64_t len) {
     // two resident blocks per SM (registers), at least 256 rows each
@@ -583,7 +613,7 @@ static cudaError_t orthonormalize_once(BlockCtx& c, float* X, int64_t ldx, int q
     }
     if (e == cudaSuccess) e = download(c, Gd, G, (size_t)q * q);
     if (e != cudaSuccess) return e;
-    bool again = false;
+    bool again = c.cgs2_always && nb > 0;
     for (int j = 0; j < q && nb > 0; ++j) {
         double cc = 0.0;
         for (int i = 0; i < nb; ++i) cc += Cf[i + (size_t)nb * j] * Cf[i + (size_t)nb * j];
@@ -667,8 +697,16 @@ static cudaError_t block_product(BlockCtx& c, bool transpose, const float* X, in
         const int per = 128 / c.tc_digits;
         for (int c0 = 0; c0 < q; c0 += per) {
             int nl = 0;
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (c.profile) {
+                auto& pool = transpose ? c.ev_rmv : c.ev_mv;
+                auto& used = transpose ? c.used_rmv : c.used_mv;
+                e0 = c.next_event(pool, used);
+                e1 = c.next_event(pool, used);
+            }
             cudaError_t e = launch_block_product_tc(h, transpose, X + (int64_t)c0 * ldx, ldx, std::min(per, q - c0),
-                                                    c.tc_digits, Y + (int64_t)c0 * ldy, ldy, c.tc_scratch, &nl);
+                                                    c.tc_digits, Y + (int64_t)c0 * ldy, ldy, c.tc_scratch, &nl, e0,
+                                                    e1);
             if (e != cudaSuccess) return e;
             c.launches += nl;
         }
@@ -780,6 +818,11 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
                0.0,
                0.0,
                0};
+    c.profile = o->profile != 0 && use_tc;
+    {
+        const char* bc = getenv("GKL_BLOCK_CGS");
+        c.cgs2_always = bc && strcmp(bc, "2") == 0;
+    }
     cudaError_t e = cudaMemsetAsync(sv.sc, 0, sizeof(DevScal), c.st);
     cudaEvent_t ev0, ev1;
     cudaEventCreate(&ev0);
@@ -788,7 +831,12 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
     std::vector<double> T(ell2, 0.0), R, S, P, sg;
     std::vector<double> Slast;
     CycleOut* ho = h->host_out;
-    int cycle = 0, restarts = 0, converged = 0, svd_fb = 0, svd_fp64 = 0, max_sweeps = 0;
+    int cycle = 0, restarts = 0, converged = 0, svd_fb = 0, svd_fp64 = 0, max_sweeps = 0, svd_unrefined = 0,
+        svd_uncontracted = 0;
+    // GKL_BLOCK_SVD=fp64: where the FP64 refinement of the projected SVD does not
+    // apply, take the FP64 Jacobi at every cycle (not only the last)
+    const char* bsv = getenv("GKL_BLOCK_SVD");
+    const bool svd_fp64_always = bsv && strcmp(bsv, "fp64") == 0;
     double maxrel = 0.0, dtheta = 0.0;
     std::vector<double> res(k, 0.0);
     auto fail = [&](const char* what) {
@@ -854,7 +902,7 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
             cudaError_t err = launch_small_svd(sv, c.st, 0);
             sv.fp32_only = 1;
             if (err != cudaSuccess) return err;
-            c.launches += 10;
+            c.launches += 12;
             err = cudaMemcpyAsync(ho, sv.co, sizeof(CycleOut), cudaMemcpyDeviceToHost, c.st);
             if (err == cudaSuccess)
                 err = cudaMemcpyAsync(&svd_fb, &sv.sc->svd_fallback, sizeof(int), cudaMemcpyDeviceToHost, c.st);
@@ -884,8 +932,10 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
             return cudaSuccess;
         };
         if ((e = upload(c, T, sv.B)) != cudaSuccess) return fail("T upload");
-        if ((e = projected(false)) != cudaSuccess) return fail("projected SVD");
-        if ((converged || cycle == o->maxit - 1) && svd_fb) {
+        if ((e = projected(svd_fp64_always)) != cudaSuccess) return fail("projected SVD");
+        if (svd_fb) ++svd_unrefined;
+        if (ho->svd_unconverged) ++svd_uncontracted;
+        if ((converged || cycle == o->maxit - 1) && svd_fb && !svd_fp64_always) {
             ++svd_fp64;
             if ((e = projected(true)) != cudaSuccess) return fail("projected SVD (FP64)");
         }
@@ -1019,6 +1069,12 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
         info->ms_total = ms;
         info->launches = c.launches + 5;
         info->svd_fallbacks = svd_fp64;
+        info->svd_clusters = svd_unrefined;  // cycles whose projected SVD could not be refined
+        info->reorth_u = svd_uncontracted;   // ... of which because the refinement did not contract
+        if (c.profile) {  // main tensor-core product kernels, summed
+            info->ms_mv = sum_event_pairs(c.ev_mv, c.used_mv, &info->n_mv);
+            info->ms_rmv = sum_event_pairs(c.ev_rmv, c.used_rmv, &info->n_rmv);
+        }
         info->jacobi_sweeps = max_sweeps;
     }
     h->last_valid = 0;  // gkl_grad works from the single-vector solvers' triplets

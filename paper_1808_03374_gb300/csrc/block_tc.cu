@@ -790,7 +790,8 @@ size_t block_tc_scratch_bytes(const gkl_handle* h, int q) {
 // Y (n x q) = A X (transpose = 0) or X' (m x q) = A^T X (transpose = 1) with D
 // digits per vector (q D <= 128).
 cudaError_t launch_block_product_tc(const gkl_handle* h, bool transpose, const float* X, int64_t ldx, int q, int D,
-                                    float* Y, int64_t ldy, void* scratch, int* nlaunch) {
+                                    float* Y, int64_t ldy, void* scratch, int* nlaunch, cudaEvent_t ev0,
+                                    cudaEvent_t ev1) {
     if (q < 1 || q * D > 128 || (D != 4 && D != 8)) return cudaErrorInvalidValue;
     const BtPlan p = plan_bt(h, q);
     uint8_t* dig = static_cast<uint8_t*>(scratch);
@@ -809,14 +810,18 @@ cudaError_t launch_block_product_tc(const gkl_handle* h, bool transpose, const f
         cudaMemsetAsync(dig, 0, p.dig_u, st);
         k_bt_digits_u<<<dim3((unsigned)p.nsub, (unsigned)q), 128, 0, st>>>(X, ldx, h->n, D, h->s, mx, dig);
         BtRmvArgs a{dig, mx, h->mu, h->d, h->w, Y, ldy, h->m, p.nstages_n, p.ntiles, q, D, err};
+        if (ev0) cudaEventRecord(ev0, st);
         k_bt_rmv<<<std::min(p.ntiles, sms), kThreadsBT, kRmvSmem, st>>>(map, a);
+        if (ev1) cudaEventRecord(ev1, st);
         if (nlaunch) *nlaunch = 3;
     } else {
         cudaMemsetAsync(dig, 0, p.dig_v, st);
         k_bt_digits_v<<<dim3((unsigned)p.nstages_m, (unsigned)q), 128, 0, st>>>(X, ldx, h->m, D, h->mu, h->d, h->w,
                                                                               mx, dig);
         BtMvArgs a{dig, Z, p.ldz, h->n, p.nblocks, p.nchunks, p.chunk_stages, p.nstages_m, q, D, err};
+        if (ev0) cudaEventRecord(ev0, st);
         k_bt_mv<<<std::min(p.nblocks * p.nchunks, sms), kThreadsBT, kMvSmem, st>>>(map, a);
+        if (ev1) cudaEventRecord(ev1, st);
         k_bt_mv_fin<<<(unsigned)((h->n * q + 255) / 256), 256, 0, st>>>(Z, p.ldz, p.nchunks, h->n, q, D, mx, h->s, Y,
                                                                         ldy);
         if (nlaunch) *nlaunch = 4;
@@ -840,7 +845,7 @@ extern "C" int gkl_matmat(gkl_handle* h, int32_t transpose, int32_t q, int32_t d
     cudaError_t e = cudaMalloc(&scratch, block_tc_scratch_bytes(h, std::min<int>(per, q)));
     for (int c0 = 0; c0 < q && e == cudaSuccess; c0 += per)
         e = launch_block_product_tc(h, transpose != 0, X + (int64_t)c0 * ldx, ldx, std::min(per, q - c0), digits,
-                                    Y + (int64_t)c0 * ldy, ldy, scratch, nullptr);
+                                    Y + (int64_t)c0 * ldy, ldy, scratch, nullptr, nullptr, nullptr);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (scratch) cudaFree(scratch);
     if (e != cudaSuccess) return cuda_err(h, e, "gkl_matmat");

@@ -37,7 +37,8 @@ enum { ABORT_NONE = 0, ABORT_BREAKDOWN = 1, ABORT_NONFINITE = 2 };
 struct CycleOut {
     int conv;
     int sweeps;
-    int pad0, pad1;
+    int svd_cluster;          // projected SVD: refinement not applied (clustered or tiny kept values)
+    int svd_unconverged;      // projected SVD: refinement applied but did not contract
     double maxrel;
     double dtheta;
     double sg[GKL_MAX_ELL];
@@ -196,8 +197,10 @@ cudaError_t launch_small_svd(const Sv& sv, cudaStream_t st, int restart_ready);
 bool block_tc_usable(const gkl_handle* h);
 bool block_tc_prepare(gkl_handle* h);
 size_t block_tc_scratch_bytes(const gkl_handle* h, int q);
+// ev0/ev1 (optional) are recorded around the main tensor-core kernel.
 cudaError_t launch_block_product_tc(const gkl_handle* h, bool transpose, const float* X, int64_t ldx, int q, int D,
-                                    float* Y, int64_t ldy, void* scratch, int* nlaunch);
+                                    float* Y, int64_t ldy, void* scratch, int* nlaunch, cudaEvent_t ev0 = nullptr,
+                                    cudaEvent_t ev1 = nullptr);
 // block form (block.cu)
 int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, float* Vout, double* resid,
               gkl_info* info);

@@ -15,10 +15,11 @@
 //     s_i  = T_ii / (1 - (R_ii + S_ii)/2),
 //     F_ij = (a s_j + b s_i) / (s_j^2 - s_i^2),  G_ij = (a s_i + b s_j) / (s_j^2 - s_i^2),
 //     a = T_ij + s_j R_ij,  b = T_ji + s_j S_ij,  F_ii = R_ii/2,  G_ii = S_ii/2.
-// The error is squared by each step (FP32 level -> FP64 level in one or two
-// steps; three are run, then the result is checked).  When two singular values are closer than FP32 can separate, or
-// one is tiny, the refinement does not apply and a full FP64 one-sided Jacobi
-// runs instead.
+// The error of a pair is squared by each step, relative to the pair's gap; four
+// steps are run, then the result is checked.  When two kept singular values are
+// closer (relative to their own size) than FP32 vectors can separate, or one is
+// tiny, the refinement does not apply and a full FP64 one-sided Jacobi runs
+// instead (the block form keeps the FP32 triplets except at its last cycle).
 #include <algorithm>
 
 #include "epilogue.cuh"
@@ -27,7 +28,8 @@
 namespace gkl {
 
 namespace {
-constexpr double kClusterGap = 1e-5;   // relative gap below which FP32 vectors are not refinable
+constexpr double kClusterGap = 1e-5;   // values below this fraction of sigma_1 are "tiny" (not refinable)
+constexpr double kClusterRel = 5e-6;   // gap / value below which an FP32 pair is not refinable
 constexpr double kRefineCheck = 1e-10;  // largest acceptable departure after the refinement steps
 }
 
@@ -214,9 +216,9 @@ __global__ void __launch_bounds__(1024) k_svd32(Sv sv) {
         __syncthreads();
         if (maxr == 0.f) break;  // no rotation in the sweep
         // Near convergence Jacobi is quadratic: a sweep that does not halve the
-        // largest remaining |cos|, already within 16x the threshold, is at FP32
+        // largest remaining |cos|, already within 2x the threshold, is at FP32
         // rounding level (the FP64 refinement that follows takes it from there).
-        if (maxr < 16.f * jtol && maxr > 0.5f * prev) break;
+        if (maxr < 2.f * jtol && maxr > 0.5f * prev) break;
         prev = maxr;
     }
     for (int c = warp; c < ell; c += nw) {
@@ -255,10 +257,14 @@ __global__ void __launch_bounds__(1024) k_svd32(Sv sv) {
         const double top = sig0[0];
         int fb = !(top > 0.0);
         const int last = min(sv.kk, ell - 1);
+        // the FP32 vectors of a pair are accurate to about eps_32 sigma / gap, so
+        // the gap is measured relative to the pair's own value
         for (int i = 1; i <= last && !fb; ++i)
-            if (sig0[i - 1] - sig0[i] <= kClusterGap * top) fb = 1;
+            if (sig0[i - 1] - sig0[i] <= kClusterRel * sig0[i - 1]) fb = 1;
         if (sig0[sv.kk - 1] <= kClusterGap * top) fb = 1;
         sv.sc->svd_fallback = fb;
+        sv.co->svd_cluster = fb;
+        sv.co->svd_unconverged = 0;
         if (fb) {
             sv.sc->n_svd_fallback += 1;
             sv.sc->n_svd_cluster += 1;
@@ -323,9 +329,10 @@ __global__ void __launch_bounds__(128) k_ref_b(Sv sv, const double* __restrict__
         if (k == j) {
             f[k] = 0.5 * R[j + j * ell];
             g[k] = 0.5 * S[j + j * ell];
-        } else if (fabs(sj - s_s[k]) <= kClusterGap * top) {
-            // unresolved pair (only possible outside the kept triplets, see
-            // k_svd32): leave it unrotated
+        } else if (fabs(sj - s_s[k]) <= kClusterRel * fmax(fabs(sj), fabs(s_s[k])) ||
+                   fmax(fabs(sj), fabs(s_s[k])) <= kClusterGap * top) {
+            // unresolved pair: too close for the FP32 vectors, or both tiny (only
+            // possible outside the refined triplets, see k_svd32): leave it unrotated
             f[k] = 0.0;
             g[k] = 0.0;
         } else {
@@ -381,6 +388,7 @@ __global__ void __launch_bounds__(256) k_svd_final(Sv sv, const double* __restri
         if (threadIdx.x == 0) {
             sv.sc->svd_fallback = 1;
             sv.sc->n_svd_fallback += 1;
+            sv.co->svd_unconverged = 1;
         }
         return;
     }
@@ -534,14 +542,16 @@ cudaError_t launch_small_svd(const Sv& sv, cudaStream_t st, int restart_ready) {
     double* V0 = U0 + ell2;
     double* U1 = V0 + ell2;
     double* V1 = U1 + ell2;
+    // four refinement steps (quadratic: an FP32 start at a tenth of the gaps
+    // reaches FP64 rounding), then the check of the result
+    for (int step = 0; step < 4; ++step) {
+        k_ref_a<<<ell, 128, 0, st>>>(sv, U0, V0);
+        k_ref_b<<<ell, 128, 0, st>>>(sv, U0, V0, U1, V1);
+        std::swap(U0, U1);
+        std::swap(V0, V1);
+    }
     k_ref_a<<<ell, 128, 0, st>>>(sv, U0, V0);
-    k_ref_b<<<ell, 128, 0, st>>>(sv, U0, V0, U1, V1);
-    k_ref_a<<<ell, 128, 0, st>>>(sv, U1, V1);
-    k_ref_b<<<ell, 128, 0, st>>>(sv, U1, V1, U0, V0);
-    k_ref_a<<<ell, 128, 0, st>>>(sv, U0, V0);
-    k_ref_b<<<ell, 128, 0, st>>>(sv, U0, V0, U1, V1);
-    k_ref_a<<<ell, 128, 0, st>>>(sv, U1, V1);  // check of the result
-    k_svd_final<<<1, 256, 0, st>>>(sv, U1, V1, restart_ready);
+    k_svd_final<<<1, 256, 0, st>>>(sv, U0, V0, restart_ready);
     if (sv.fp32_only) {
         k_svd_take32<<<1, 256, 0, st>>>(sv, restart_ready);
         return cudaGetLastError();

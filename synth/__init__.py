@@ -196,7 +196,7 @@ CONFIGS = {
     "block_50k_x_500k": Workload(
         "block_50k_x_500k",
         GenoSpec(n=50_000, m=500_000, n_pops=10, admixture=True, miss_rate=0.01, seed=0x5EED0003),
-        k=20, ell=128, reorth="full", precision="bf16x2_block", tol=1e-6, extra={"block": 32}),
+        k=20, ell=128, reorth="full", precision="block", tol=1e-6, extra={"block": 16, "k_keep": 48}),
     "grad_20k_x_200k": Workload(
         "grad_20k_x_200k",
         GenoSpec(n=20_000, m=200_000, n_pops=5, admixture=True, miss_rate=0.0, seed=0x5EED0004),
@@ -205,7 +205,7 @@ CONFIGS = {
         "large_200k_x_1m",
         GenoSpec(n=200_000, m=1_000_000, n_pops=20, admixture=True,
                  base=("beta", 0.5, 2.0, 0.01, 0.5), miss_rate=0.01, seed=0x5EED0005),
-        k=20, ell=128, reorth="full", precision="bf16x2_block", tol=1e-6, extra={"block": 32}),
+        k=20, ell=128, reorth="full", precision="block", tol=1e-6, extra={"block": 16, "k_keep": 48}),
 }
 
 
