@@ -63,7 +63,12 @@ typedef struct gkl_handle gkl_handle;
 #define GKL_BLOCK 2
 /* the same with 4-digit (16-bit fixed point, the precision of a split hi+lo
  * BF16 pair) products during the iteration, 32 vectors per tensor-core pass;
- * the final Rayleigh-Ritz step and the residuals use 8 digits. */
+ * the final Rayleigh-Ritz step and the residuals use 8 digits.
+ * Environment (block forms): GKL_BLOCK_PRODUCTS=simt runs the products on the
+ * SIMT kernels; GKL_BLOCK_CGS=2 always runs two Gram-Schmidt passes (default:
+ * a second pass only where the first removed more than half of a column's
+ * squared norm); GKL_BLOCK_SVD=fp64 takes the FP64 Jacobi in every cycle whose
+ * projected SVD cannot be refined (default: only in the last cycle). */
 #define GKL_BLOCK16 3
 
 /* reorthogonalisation strategy (section 3) */
