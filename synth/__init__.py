@@ -63,6 +63,9 @@ def _lib():
             lib.synth_normal_vec.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, ctypes.c_void_p]
             lib.synth_uniform_vec.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64,
                                               ctypes.c_double, ctypes.c_double, ctypes.c_void_p]
+            lib.synth_paper_model.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                              ctypes.c_double, ctypes.c_double, ctypes.c_uint64, ctypes.c_void_p]
+            lib.synth_paper_model.restype = ctypes.c_int
             _LIB = lib
     return _LIB
 
@@ -143,6 +146,40 @@ def genotypes(spec: GenoSpec, out: np.ndarray | None = None) -> Genotypes:
     if lib.synth_pack(ctypes.byref(p), f.ctypes.data, q.ctypes.data, out.ctypes.data) != 0:
         raise ValueError("bad genotype spec")
     return Genotypes(spec, out, f, q)
+
+
+@dataclass(frozen=True)
+class ModelSpec:
+    """The paper's synthetic genotype model (section 2, Algorithm 1): m markers
+    by n patients, r admixture sub-blocks, nsignal_frac * m * n signal draws and
+    round(rkins * m) duplicated marker rows (see synth.c)."""
+    n: int
+    m: int
+    r: int = 10
+    nsignal_frac: float = 1.0
+    rkins: float = 0.017
+    seed: int = 0x5EED0006
+
+    @property
+    def stride(self) -> int:
+        return padded_stride(self.n)
+
+
+# The matrix size and parameters of the paper's Fig. empirical-spectrum and
+# Table 3 (41,505 markers x 81,700 patients, r = 10, nsignal = mn, rkins = 0.017).
+PAPER_MODEL = ModelSpec(n=81_700, m=41_505)
+
+
+def paper_model(spec: ModelSpec, out: np.ndarray | None = None) -> Genotypes:
+    """Draw the packed matrix of the paper's model (deterministic in spec.seed)."""
+    if out is None:
+        out = np.empty((spec.m, spec.stride), dtype=np.uint8)
+    assert out.shape == (spec.m, spec.stride) and out.dtype == np.uint8 and out.flags.c_contiguous
+    rc = _lib().synth_paper_model(spec.n, spec.m, spec.stride, spec.r, spec.nsignal_frac * spec.m * spec.n,
+                                  spec.rkins, spec.seed, out.ctypes.data)
+    if rc != 0:
+        raise ValueError("bad model spec")
+    return Genotypes(spec, out, np.zeros((0, spec.m)), np.zeros((spec.n, 0)))
 
 
 def normal_vec(seed: int, stream: int, length: int) -> np.ndarray:

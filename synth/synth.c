@@ -69,7 +69,10 @@ enum {
     ST_POP = 2,   /* per-(pop,SNP) perturbation  ctr = (j, k, ST, draw) */
     ST_ANC = 3,   /* per-sample ancestry         ctr = (i, k, ST, draw) */
     ST_GENO = 4,  /* per-entry genotype          ctr = (i, j, ST, 0)    */
-    ST_VEC = 5    /* free-standing vectors       ctr = (i, stream, ST, draw) */
+    ST_VEC = 5,   /* free-standing vectors       ctr = (i, stream, ST, draw) */
+    ST_MODEL_BLK = 6,  /* paper model: sub-block b    ctr = (b, 0, ST, draw) */
+    ST_MODEL_SIG = 7,  /* paper model: entry (j, i)   ctr = (i, j, ST, 0) */
+    ST_MODEL_KIN = 8   /* paper model: row copy c     ctr = (c, 0, ST, 0) */
 };
 
 static inline ctr4 draw(uint64_t seed, uint32_t a, uint32_t b, uint32_t st, uint32_t d) {
@@ -222,4 +225,65 @@ void synth_uniform_vec(uint64_t seed, uint32_t stream, int64_t len, double lo, d
         ctr4 r = draw(seed, (uint32_t)i, stream, ST_VEC, 0x80000000u | (uint32_t)(i >> 32));
         out[i] = lo + (hi - lo) * (u53(r.w[0], r.w[1]) - 0x1p-53);
     }
+}
+
+/* The synthetic genotype model of section 2 (Algorithm 1) of the paper, in the
+ * SNP-major packed layout: m markers (rows of the paper's matrix, SNPs here)
+ * by n patients (samples).
+ *  1. r sub-blocks: a marker range and a patient range, each the span between
+ *     two uniform picks, set to one value k in {0, 1, 2}; later blocks overwrite
+ *     earlier ones.
+ *  2. "signal": nsignal draws, each setting a uniformly chosen entry to a
+ *     uniform value in {0, 1, 2}.  Written per entry: an entry is hit with
+ *     probability 1 - (1 - 1/(mn))^nsignal and then holds a uniform value,
+ *     which is the distribution of each entry under the sequential draws.
+ *  3. kinship: round(rkins m) times, a uniformly chosen marker row is replaced
+ *     by a copy of another uniformly chosen row, in order.
+ * No missing codes; padding samples are code 3. */
+static inline uint32_t below(uint32_t x, uint32_t bound) { return (uint32_t)(((uint64_t)x * bound) >> 32); }
+
+int synth_paper_model(int64_t n, int64_t m, int64_t stride, int32_t r, double nsignal, double rkins, uint64_t seed,
+                      uint8_t *packed) {
+    if (stride * 4 < n || stride % 16 != 0 || n <= 0 || m <= 0 || n > 0xFFFFFFFFLL || m > 0xFFFFFFFFLL) return -1;
+    if (r < 0 || r > 4096) return -1;
+    int64_t *blk = (int64_t *)malloc(sizeof(int64_t) * 5 * (size_t)(r > 0 ? r : 1));
+    if (!blk) return -2;
+    for (int32_t b = 0; b < r; ++b) {
+        ctr4 x = draw(seed, (uint32_t)b, 0, ST_MODEL_BLK, 0);
+        ctr4 y = draw(seed, (uint32_t)b, 0, ST_MODEL_BLK, 1);
+        int64_t j1 = below(x.w[1], (uint32_t)m), j2 = below(x.w[2], (uint32_t)m);
+        int64_t i1 = below(x.w[3], (uint32_t)n), i2 = below(y.w[0], (uint32_t)n);
+        blk[5 * b + 0] = below(x.w[0], 3u);
+        blk[5 * b + 1] = j1 < j2 ? j1 : j2;
+        blk[5 * b + 2] = j1 < j2 ? j2 : j1;
+        blk[5 * b + 3] = i1 < i2 ? i1 : i2;
+        blk[5 * b + 4] = i1 < i2 ? i2 : i1;
+    }
+    const double mn = (double)n * (double)m;
+    const double p_hit = nsignal > 0.0 ? -expm1(nsignal * log1p(-1.0 / mn)) : 0.0;
+    const double hit_thr = p_hit * 4294967296.0;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t j = 0; j < m; ++j) {
+        uint8_t *row = packed + j * stride;
+        memset(row, 0xFF, (size_t)stride);
+        for (int64_t i = 0; i < n; ++i) {
+            unsigned code = 0u;
+            for (int32_t b = 0; b < r; ++b)
+                if (j >= blk[5 * b + 1] && j <= blk[5 * b + 2] && i >= blk[5 * b + 3] && i <= blk[5 * b + 4])
+                    code = (unsigned)blk[5 * b];
+            ctr4 x = draw(seed, (uint32_t)i, (uint32_t)j, ST_MODEL_SIG, 0);
+            if ((double)x.w[0] < hit_thr) code = below(x.w[1], 3u);
+            const int sh = 2 * (int)(i & 3);
+            uint8_t *bp = row + (i >> 2);
+            *bp = (uint8_t)((*bp & ~(3u << sh)) | (code << sh));
+        }
+    }
+    const int64_t nkins = (int64_t)llround(rkins * (double)m);
+    for (int64_t c = 0; c < nkins; ++c) {
+        ctr4 x = draw(seed, (uint32_t)c, 0, ST_MODEL_KIN, 0);
+        const int64_t dst = below(x.w[0], (uint32_t)m), src = below(x.w[1], (uint32_t)m);
+        if (dst != src) memcpy(packed + dst * stride, packed + src * stride, (size_t)stride);
+    }
+    free(blk);
+    return 0;
 }

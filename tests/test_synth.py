@@ -92,3 +92,54 @@ def test_vectors():
     assert abs(np.corrcoef(a, b)[0, 1]) < 0.02
     u = synth.uniform_vec(1, 2, 100_000, 0.5, 1.5)
     assert u.min() >= 0.5 and u.max() < 1.5 and abs(u.mean() - 1.0) < 0.01
+
+
+# ---- the paper's synthetic model (section 2, Algorithm 1) --------------------
+
+def _model_draw(seed, a, b, st, d):
+    return synth.philox4x32_10((a, b, st, d), (seed & 0xFFFFFFFF, seed >> 32))
+
+
+def _below(x, bound):
+    return (x * bound) >> 32
+
+
+def _codes(g):
+    return np.stack([(g.packed >> (2 * t)) & 3 for t in range(4)], -1).reshape(g.m, -1)
+
+
+def test_paper_model_blocks_and_kinship_exact():
+    """With no signal draws the matrix is the admixture sub-blocks (later ones on
+    top) followed by the ordered row copies: rebuilt here from the same
+    counter-based draws, entry for entry."""
+    spec = synth.ModelSpec(n=203, m=97, r=6, nsignal_frac=0.0, rkins=0.08, seed=0x1234_5678_9ABC)
+    g = synth.paper_model(spec)
+    n, m = spec.n, spec.m
+    A = np.zeros((m, n), dtype=np.int64)
+    for b in range(spec.r):
+        x = _model_draw(spec.seed, b, 0, 6, 0)
+        y = _model_draw(spec.seed, b, 0, 6, 1)
+        k = _below(x[0], 3)
+        j1, j2 = sorted((_below(x[1], m), _below(x[2], m)))
+        i1, i2 = sorted((_below(x[3], n), _below(y[0], n)))
+        A[j1:j2 + 1, i1:i2 + 1] = k
+    for c in range(round(spec.rkins * m)):
+        x = _model_draw(spec.seed, c, 0, 8, 0)
+        A[_below(x[0], m)] = A[_below(x[1], m)].copy()
+    codes = _codes(g)
+    assert np.array_equal(codes[:, :n], A)
+    assert np.all(codes[:, n:] == 3)
+
+
+def test_paper_model_signal_distribution():
+    """Each entry is hit by the signal draws with probability 1 - (1 - 1/mn)^nsignal
+    and then holds a uniform value in {0, 1, 2}: with no sub-blocks the share of
+    zeros is (1 - p) + p/3 and of ones and twos p/3 each."""
+    spec = synth.ModelSpec(n=400, m=300, r=0, nsignal_frac=1.0, rkins=0.0, seed=77)
+    codes = _codes(synth.paper_model(spec))[:, :spec.n]
+    mn = spec.n * spec.m
+    p = 1.0 - (1.0 - 1.0 / mn) ** mn
+    share = np.bincount(codes.ravel(), minlength=3) / mn
+    sd = np.sqrt(p / 3 * (1 - p / 3) / mn)
+    assert abs(share[1] - p / 3) < 6 * sd and abs(share[2] - p / 3) < 6 * sd
+    assert abs(share[0] - (1 - p + p / 3)) < 12 * sd
