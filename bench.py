@@ -465,6 +465,64 @@ def run_paper_model(args):
     return 0
 
 
+def run_compare(args):
+    """One workload of synth.CONFIGS: the FP32 single-vector solve (PARTIAL) and
+    the block form (b=16, l=128, k_keep=48), each once after the matrix is on
+    the device; times, pair counts, true residuals from the 8-digit block
+    products, singular-value agreement, and the sigma-part gradient
+    (d sum_i sigma_i^2 / dw) after the FP32 solve.  One JSON line."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1808_03374_gb300 import build, gkl
+    build()
+    w = synth.CONFIGS[args.compare]
+    t0 = time.time()
+    g = synth.genotypes(w.geno)
+    gen_s = time.time() - t0
+    t0 = time.time()
+    h = gkl.GKL(torch.from_numpy(g.packed).cuda(), g.n)
+    torch.cuda.synchronize()
+    init_s = time.time() - t0
+
+    def true_resid(res):
+        worst = 0.0
+        for c0 in range(0, res.U.shape[1], 16):  # 16 vectors per 8-digit pass
+            Ut = res.U[:, c0:c0 + 16].T.contiguous().float()
+            Vt = res.V[:, c0:c0 + 16].T.contiguous().float()
+            Z, Y = h.matmat(Ut, transpose=True), h.matmat(Vt)
+            sg = torch.tensor(res.sigma[c0:c0 + 16], device="cuda", dtype=torch.float32)[:, None]
+            worst = max(worst, torch.linalg.norm((Z - sg * Vt).double(), dim=1).max().item(),
+                        torch.linalg.norm((Y - sg * Ut).double(), dim=1).max().item())
+        return worst / res.sigma[0]
+
+    def timed(**kw):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = h.svd(**kw)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, r
+
+    out = {"workload": args.compare, "n": g.n, "m": g.m, "packed_bytes": int(g.packed.nbytes),
+           "generated_s": gen_s, "to_device_and_init_s": init_s}
+    tb, rb = timed(k=w.k, ell=128, precision="block", block=16, k_keep=48, tol=1e-6, maxit=500, seed=7)
+    out["block"] = {"time_s": tb, "vector_pairs": int(rb.info["matvec_pairs"]), "restarts": int(rb.info["restarts"]),
+                    "converged": bool(rb.info["converged"]), "true_max_rel_resid": true_resid(rb)}
+    tf, rf = timed(k=w.k, ell=50, reorth="partial", precision="fp32", tol=1e-6, maxit=3000, seed=7)
+    out["fp32_partial"] = {"time_s": tf, "pairs": int(rf.info["matvec_pairs"]), "restarts": int(rf.info["restarts"]),
+                           "converged": bool(rf.info["converged"]), "reported_max_rel_resid": rf.info["max_rel_resid"],
+                           "true_max_rel_resid": true_resid(rf)}
+    out["sigma_max_rel_diff"] = float(np.max(np.abs(rb.sigma - rf.sigma)) / rf.sigma[0])
+    out["sigma_top5"] = [float(x) for x in rf.sigma[:5]]
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    _, gw = h.grad(sigma_bar=2.0 * rf.sigma, want_s=False, dtype=torch.float32)
+    torch.cuda.synchronize()
+    out["grad_w_sigma_part"] = {"time_s": time.perf_counter() - t, "norm": float(gw.double().norm().item())}
+    print(json.dumps({"compare": out}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -478,7 +536,11 @@ def main():
                     help="only warm up and run one block-form solve (for profiler launch lists)")
     ap.add_argument("--paper-model", action="store_true",
                     help="the paper's synthetic model at its Table 3 size: solvers side by side (one JSON line)")
+    ap.add_argument("--compare", default=None,
+                    help="a workload of synth.CONFIGS: FP32 solve and block form side by side (one JSON line)")
     args = ap.parse_args()
+    if args.compare:
+        return run_compare(args)
     if args.profile_block:
         return run_block_profile(args)
     if args.paper_model:
