@@ -39,6 +39,25 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def reduce_over_ranks(x: float, dist, device, op: str) -> float:
+    """x combined over all ranks ("max" or "sum") through a collective of the
+    process group (NCCL on the GPU machine, gloo in the CPU tests)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_throughput(units_local: float, ms_local: float, dist=None, device="cpu") -> tuple[float, float]:
+    """Whole-job throughput of independent replicas: the units of all ranks
+    over the slowest rank's time.  Returns (units per second, max ms)."""
+    if dist is None:
+        return units_local / (ms_local / 1e3), ms_local
+    ms = reduce_over_ranks(ms_local, dist, device, "max")
+    units = reduce_over_ranks(units_local, dist, device, "sum")
+    return units / (ms / 1e3), ms
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -239,13 +258,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         if pg:
             pg.barrier()
-    ms = e0.elapsed_time(e1)
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
     pairs = sum(i["matvec_pairs"] for i in infos)
-    value = world * pairs / (ms / 1e3)
+    value, ms = job_throughput(pairs, e0.elapsed_time(e1), pg, "cuda")
     clocks = clk.summary()
 
     # roofline of the dominant kernel, from the CUDA events recorded around each
@@ -292,7 +306,7 @@ def run_ours(args):
             e2e_pairs += rr.info["matvec_pairs"]
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        e2e = {"value": world * e2e_pairs / dt, "unit": "pairs/s", "h2d_bytes_per_step": int(packed_host.numel()),
+        e2e = {"value": job_throughput(e2e_pairs, dt * 1e3, pg, "cuda")[0], "unit": "pairs/s", "h2d_bytes_per_step": int(packed_host.numel()),
                "d2h_bytes_per_step": int(Uh.numel() * Uh.element_size() + Vh.numel() * Vh.element_size() + 16 * w.k),
                "steps": e2e_steps}
 
