@@ -480,7 +480,6 @@ struct BlockCtx {
     int launches;
     int deflations;
     int cgs_second;    // orthonormalisations that needed a second Gram-Schmidt pass
-    double ms_mv, ms_rmv;
     int64_t products;
     // profile: CUDA events around each main tensor-core kernel (pairs), kept
     // until the solve's final synchronisation
@@ -815,8 +814,6 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
                0,
                0,
                0,
-               0.0,
-               0.0,
                0};
     c.profile = o->profile != 0 && use_tc;
     {

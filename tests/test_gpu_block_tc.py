@@ -99,3 +99,36 @@ def test_matmat_arguments(gk):
         h.matmat(X, digits=5)
     with pytest.raises(gk.GKLError):
         h.matmat(torch.zeros((33, 50), device="cuda"))
+
+
+def test_full_size_block_products_sampled(gk):
+    """10,000 x 100,000 workload (2% missing, 5-population admixture), 16
+    vectors in 8 digits (the block solver's launch configuration) and 32 in 4:
+    sampled outputs of both products against the oracle's one-by-one rows and
+    columns, within the elementwise bound of the header."""
+    import torch
+    w = synth.CONFIGS["fp32_pro_10k_x_100k"]
+    g = synth.genotypes(w.geno)
+    M = oracle_matrix(g)
+    h = gk.GKL(to_dev(g.packed), g.n)
+    rng = np.random.default_rng(1)
+    rows = np.unique(np.r_[0, g.n - 1, rng.integers(0, g.n, 24)])
+    cols = np.unique(np.r_[0, g.m - 1, rng.integers(0, g.m, 24)])
+    dw = M.d
+    for q, digits in ((16, 8), (32, 4)):
+        U = np.stack([synth.normal_vec(41, c, g.n) for c in range(q)]).astype(np.float32)
+        V = np.stack([synth.normal_vec(43, c, g.m) for c in range(q)]).astype(np.float32)
+        X = h.matmat(torch.tensor(U, device="cuda"), transpose=True, digits=digits).double().cpu().numpy()
+        Y = h.matmat(torch.tensor(V, device="cuda"), digits=digits).double().cpu().numpy()
+        for c in range(q):
+            u = U[c].astype(np.float64)
+            v = V[c].astype(np.float64)
+            xo = M.rmatvec_cols(u, cols)
+            yo = M.matvec_rows(v, rows)
+            bx = 2.0 ** -23 * np.abs(xo) + 2 * dw[cols] * (2.0 ** -24 * np.abs(u).sum() +
+                                                        g.n * 2.0 ** -(4 * digits + 1) * pow2_at_least(u * (1 + 2.0 ** -20)))
+            vt = dw * v
+            S = pow2_at_least(np.maximum(np.abs(vt), np.abs(M.mu * vt)) * (1 + 2.0 ** -20))
+            by = 2.0 ** -23 * np.abs(yo) + (2.0 ** -20 * np.abs(vt).sum() + 3 * g.m * 2.0 ** -(4 * digits + 1) * S)
+            assert np.all(np.abs(X[c][cols] - xo) <= bx), (q, digits, c)
+            assert np.all(np.abs(Y[c][rows] - yo) <= by), (q, digits, c)
