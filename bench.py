@@ -537,6 +537,23 @@ def run_compare(args):
     return 0
 
 
+def run_fp32_profile(args):
+    """One FP32 solve of the benchmark step at the benchmark workload, right
+    after the handle is set up (for launch lists; no warm-up solves, so the
+    profiler skips only the set-up kernels); prints one line."""
+    import torch
+    from paper_1808_03374_gb300 import build, gkl
+    build()
+    w, g = make_inputs()
+    h = gkl.GKL(torch.from_numpy(g.packed).cuda(), g.n)
+    torch.cuda.synchronize()
+    r = h.svd(k=w.k, ell=w.ell, reorth=w.reorth, precision=w.precision, tol=w.tol, maxit=2000, seed=7)
+    torch.cuda.synchronize()
+    print(json.dumps({"fp32_profile": WORKLOAD, "launches_per_solve": r.info["launches"],
+                      "ms": r.info["ms_total"], "pairs": r.info["matvec_pairs"]}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -548,6 +565,8 @@ def main():
     ap.add_argument("--no-block", action="store_true", help="skip the block-form comparison")
     ap.add_argument("--profile-block", action="store_true",
                     help="only warm up and run one block-form solve (for profiler launch lists)")
+    ap.add_argument("--profile-fp32", action="store_true",
+                    help="only set up and run one FP32 solve of the benchmark step (for profiler launch lists)")
     ap.add_argument("--paper-model", action="store_true",
                     help="the paper's synthetic model at its Table 3 size: solvers side by side (one JSON line)")
     ap.add_argument("--compare", default=None,
@@ -557,6 +576,8 @@ def main():
         return run_compare(args)
     if args.profile_block:
         return run_block_profile(args)
+    if args.profile_fp32:
+        return run_fp32_profile(args)
     if args.paper_model:
         return run_paper_model(args)
     if args.impl == "reference":
