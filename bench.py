@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import argparse
 import csv
+import ctypes
 import hashlib
 import io
 import json
@@ -169,6 +170,8 @@ def cpu_baseline_sample(w, g, budget_s=15.0, max_pairs=40):
     import synth
     M = oracle.Matrix.from_packed(g.packed, g.n)
     v = synth.normal_vec(77, 0, g.m)
+    # the oracle and the generator share one OpenMP runtime in this process
+    ctypes.CDLL("libgomp.so.1").omp_set_num_threads(args.cpu_threads)
     pairs, t0 = 0, time.perf_counter()
     while pairs < max_pairs:
         u = M.matvec(v)
@@ -554,6 +557,65 @@ def run_fp32_profile(args):
     return 0
 
 
+def run_cpu_pairs(args):
+    """Seconds per A.v + A^T.u pair of the FP64 CPU oracle on one workload (a
+    bounded sample on --cpu-threads OpenMP threads; the matrix is generated on
+    all cores first); with --cpu-solve also one full oracle solve with the
+    workload's settings."""
+    import numpy as np
+    import oracle
+    import synth
+    w = synth.CONFIGS[args.cpu_pairs]
+    t0 = time.perf_counter()
+    g = synth.genotypes(w.geno)
+    gen_s = time.perf_counter() - t0
+    M = oracle.Matrix.from_packed(g.packed, g.n)
+    v = synth.normal_vec(77, 0, g.m)
+    # the oracle and the generator share one OpenMP runtime in this process
+    ctypes.CDLL("libgomp.so.1").omp_set_num_threads(args.cpu_threads)
+    pairs, t0 = 0, time.perf_counter()
+    while pairs < args.max_pairs:
+        u = M.matvec(v)
+        u /= np.linalg.norm(u)
+        v = M.rmatvec(u)
+        v /= np.linalg.norm(v)
+        pairs += 1
+        if time.perf_counter() - t0 > args.budget:
+            break
+    per_pair = (time.perf_counter() - t0) / pairs
+    out = {"workload": args.cpu_pairs, "n": g.n, "m": g.m, "threads": args.cpu_threads,
+           "generated_s": gen_s, "pairs_timed": pairs, "s_per_pair": per_pair}
+    if args.cpu_solve:
+        t0 = time.perf_counter()
+        r = oracle.gkl(M, k=w.k, ell=w.ell, tol=w.tol, v0=synth.normal_vec(5, 0, g.m), maxit=2000)
+        out["full_solve"] = {"s": time.perf_counter() - t0, "pairs": int(getattr(r, "pairs", -1)),
+                             "converged": bool(r.converged)}
+    print(json.dumps({"cpu_pairs": out}), flush=True)
+    return 0
+
+
+def run_cpu_table(args):
+    """The FP64 CPU oracle per pair at the workloads whose generation and
+    timing fit about half a minute each, on all host cores and on one core,
+    and one full oracle solve of the small workload; each measurement in its
+    own process."""
+    cores = os.cpu_count() or 1
+    plan = [("fp64_full_1k_x_10k", cores, True), ("fp64_full_1k_x_10k", 1, False),
+            ("fp32_pro_10k_x_100k", cores, False), ("fp32_pro_10k_x_100k", 1, False),
+            ("grad_20k_x_200k", cores, False), ("grad_20k_x_200k", 1, False)]
+    rows = []
+    for name, threads, solve in plan:
+        cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-pairs", name, "--cpu-threads", str(threads),
+               "--max-pairs", "3", "--budget", "10"] + (["--cpu-solve"] if solve else [])
+        env = {k: v for k, v in os.environ.items() if k != "OMP_NUM_THREADS"}
+        res = subprocess.run(cmd, env=env, capture_output=True, text=True, cwd=ROOT)
+        line = [x for x in res.stdout.splitlines() if x.startswith("{")]
+        rows.append(json.loads(line[-1])["cpu_pairs"] if line else {"workload": name, "threads": threads,
+                                                                      "error": res.stderr[-300:]})
+    print(json.dumps({"cpu_table": {"host_cores": cores, "rows": rows}}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -569,11 +631,22 @@ def main():
                     help="only set up and run one FP32 solve of the benchmark step (for profiler launch lists)")
     ap.add_argument("--paper-model", action="store_true",
                     help="the paper's synthetic model at its Table 3 size: solvers side by side (one JSON line)")
+    ap.add_argument("--cpu-table", action="store_true",
+                    help="the FP64 CPU oracle per pair at several workloads, all cores and one core (one JSON line)")
+    ap.add_argument("--cpu-pairs", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-solve", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-threads", type=int, default=os.cpu_count() or 1, help=argparse.SUPPRESS)
+    ap.add_argument("--max-pairs", type=int, default=3, help=argparse.SUPPRESS)
+    ap.add_argument("--budget", type=float, default=20.0, help=argparse.SUPPRESS)
     ap.add_argument("--compare", default=None,
                     help="a workload of synth.CONFIGS: FP32 solve and block form side by side (one JSON line)")
     args = ap.parse_args()
     if args.compare:
         return run_compare(args)
+    if args.cpu_table:
+        return run_cpu_table(args)
+    if args.cpu_pairs:
+        return run_cpu_pairs(args)
     if args.profile_block:
         return run_block_profile(args)
     if args.profile_fp32:
