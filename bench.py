@@ -170,8 +170,6 @@ def cpu_baseline_sample(w, g, budget_s=15.0, max_pairs=40):
     import synth
     M = oracle.Matrix.from_packed(g.packed, g.n)
     v = synth.normal_vec(77, 0, g.m)
-    # the oracle and the generator share one OpenMP runtime in this process
-    ctypes.CDLL("libgomp.so.1").omp_set_num_threads(args.cpu_threads)
     pairs, t0 = 0, time.perf_counter()
     while pairs < max_pairs:
         u = M.matvec(v)
