@@ -122,6 +122,9 @@ struct MvPlan {
     int rows_per_chunk;
     int64_t ldp;        // leading dimension of A.v partials
     size_t bytes_fp64;  // scratch bytes needed (FP64)
+    // FP32 A.v (pair-table kernel): threads a block (words of a sample tile), tiles, chunks, rows a chunk
+    int pair_threads, pair_tiles, pair_chunks, pair_rpc;
+    int mv_chunks(bool fp32) const { return fp32 ? pair_chunks : chunks; }
 };
 MvPlan plan_products(const gkl_handle* h);
 

@@ -85,7 +85,7 @@ extern "C" int gkl_matvec_noalloc(const uint8_t* packed, int64_t n, int64_t m, i
 
     const gkl::MvPlan p = gkl::plan_products(&h);
     const size_t elem = prec == GKL_FP64 ? sizeof(double) : sizeof(float);
-    const size_t need = ((size_t)p.chunks * (size_t)p.ldp + (size_t)m * 4) * elem;
+    const size_t need = ((size_t)p.mv_chunks(prec == GKL_FP32) * (size_t)p.ldp + (size_t)m * 4) * elem;
     if (need > kStaticScratchBytes)
         return set_err(nullptr, GKL_ERR_ARG,
                        "gkl_matvec_noalloc: n=%lld, m=%lld needs %zu bytes of scratch, above its static maximum of "

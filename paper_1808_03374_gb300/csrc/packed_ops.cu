@@ -10,6 +10,7 @@
 // partial sums are combined in a fixed order by a second kernel, so results
 // are deterministic.
 #include <algorithm>
+#include <mutex>
 
 #include "epilogue.cuh"
 #include "gkl_internal.cuh"
@@ -85,7 +86,31 @@ MvPlan plan_products(const gkl_handle* h) {
     p.rows_per_chunk = (int)rpc;
     p.chunks = (int)((h->m + rpc - 1) / rpc);
     p.ldp = p.nwords * 16;
-    size_t mv = (size_t)p.chunks * (size_t)p.ldp + (size_t)h->m * 4;  // partials + LUT
+    // FP32 A.v: the block width (a multiple of 32 words) and chunking that give
+    // the busiest SM the fewest word-rows, one wave at the kernel's residency of
+    // 64 registers a thread; every block covers at least one 256-row batch.
+    {
+        double best = 0.0;
+        for (int nt = 256; nt >= 128; nt -= 32) {
+            const int per_sm = 65536 / (64 * nt);
+            const int64_t tiles = (p.nwords + nt - 1) / nt;
+            int64_t chunks = std::max<int64_t>(1, (int64_t)per_sm * std::max(1, h->num_sms) / tiles);
+            int64_t rpc = (h->m + chunks - 1) / chunks;
+            rpc = std::max<int64_t>(rpc, 256);
+            rpc = (rpc + 7) / 8 * 8;
+            chunks = (h->m + rpc - 1) / rpc;
+            const int64_t blocks_sm = (tiles * chunks + std::max(1, h->num_sms) - 1) / std::max(1, h->num_sms);
+            const double load = (double)blocks_sm * (double)rpc * (double)nt;
+            if (best == 0.0 || load < 0.99 * best) {
+                best = load;
+                p.pair_threads = nt;
+                p.pair_tiles = (int)tiles;
+                p.pair_chunks = (int)chunks;
+                p.pair_rpc = (int)rpc;
+            }
+        }
+    }
+    size_t mv = (size_t)std::max(p.chunks, p.pair_chunks) * (size_t)p.ldp + (size_t)h->m * 4;  // partials + LUT
     size_t rmv = 2 * (size_t)p.tiles * (size_t)h->m;
     size_t tc = h->aux ? rmv_mma_scratch_bytes(h) : 0;
     if (h->tc_state > 0) tc = std::max(tc, rmv_tc_scratch_bytes(h));
@@ -163,98 +188,122 @@ __global__ void __launch_bounds__(kThreads) k_mv_part(const uint8_t* __restrict_
 //     O = ((W_a >> 2) & 0x33..) | (W_b & 0xCC..)    is c_a + 4 c_b of sample 2k+1.
 // All lanes of a warp read the same 16-entry table, which spans 16 banks, so
 // every lookup is a single conflict-free shared-memory wavefront.
-constexpr int kPairBatch = 64;  // row pairs staged per batch (128 rows)
+//
+// The tables of four consecutive pairs fill one 256-byte-aligned group, so the
+// shared address of a lookup is one byte-permute: byte 0 = 4 x index (from the
+// code words), bytes 1-3 = the group's base; the pair within the group is the
+// load's immediate offset.  Tables are built for a batch of 128 pairs (256
+// rows) while the previous batch is consumed, into the other of two buffers:
+// one barrier per batch.  Adjacent samples accumulate with paired FP32 adds.
+constexpr int kPairBatch = 128;                  // row pairs per table batch
+constexpr int kPairRows = 2 * kPairBatch;        // 256 rows
+constexpr int kPairTab = kPairBatch * 16;        // floats per table buffer (8 KB)
+constexpr int kPairMaxThreads = 256;
 
-__global__ void __launch_bounds__(kThreads) k_mv_pair(const uint8_t* __restrict__ packed, int64_t stride,
-                                                      int64_t nwords, int64_t m, int rpc,
-                                                      const float* __restrict__ lut, float* __restrict__ part,
-                                                      int64_t ldp) {
-    __shared__ float tab[kPairBatch * 16];
-    __shared__ __align__(16) float lrow[2 * kPairBatch * 4];
-    static_assert(2 * kPairBatch * 4 == 2 * kThreads, "one float2 of per-SNP table rows per thread");
-    const int64_t word = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+template <int OFF>
+__device__ __forceinline__ float lds_f32(uint32_t a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1+%2];\n" : "=f"(v) : "r"(a), "n"(OFF));
+    return v;
+}
+
+// Four lookups (samples 4b .. 4b+3 of one pair) for b = 0..3, pair Q of the group at gb.
+template <int Q>
+__device__ __forceinline__ void pair_lookups(uint32_t wa, uint32_t wb, uint32_t gb, float2 (&acc)[8]) {
+    const uint32_t e = (wa & 0x33333333u) | ((wb & 0x33333333u) << 2);
+    const uint32_t o = ((wa >> 2) & 0x33333333u) | (wb & 0xCCCCCCCCu);
+    // bytes of eL hold 4 x nibbles 0, 2, 4, 6 of e (samples 0, 4, 8, 12), bytes of
+    // eH 4 x nibbles 1, 3, 5, 7 (samples 2, 6, 10, 14); likewise o (odd samples)
+    const uint32_t eL = (e << 2) & 0x3C3C3C3Cu, eH = (e >> 2) & 0x3C3C3C3Cu;
+    const uint32_t oL = (o << 2) & 0x3C3C3C3Cu, oH = (o >> 2) & 0x3C3C3C3Cu;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const uint32_t sel = 0x7650u | (uint32_t)b;
+        const float x0 = lds_f32<Q * 64>(__byte_perm(eL, gb, sel));
+        const float x1 = lds_f32<Q * 64>(__byte_perm(oL, gb, sel));
+        const float x2 = lds_f32<Q * 64>(__byte_perm(eH, gb, sel));
+        const float x3 = lds_f32<Q * 64>(__byte_perm(oH, gb, sel));
+        acc[2 * b] = __fadd2_rn(acc[2 * b], make_float2(x0, x1));
+        acc[2 * b + 1] = __fadd2_rn(acc[2 * b + 1], make_float2(x2, x3));
+    }
+}
+
+__global__ void __launch_bounds__(kPairMaxThreads, 4)
+    k_mv_pair(const uint8_t* __restrict__ packed, int64_t stride, int64_t nwords, int64_t m, int rpc,
+              const float* __restrict__ lut, float* __restrict__ part, int64_t ldp) {
+    // two table buffers, each starting on a 256-byte boundary of the shared window
+    __shared__ __align__(16) float tabs[2 * kPairTab + 64];
+    const uint32_t tabs_sh = (uint32_t)__cvta_generic_to_shared(tabs);
+    const uint32_t tb0 = (tabs_sh + 255u) & ~255u;
+    const int nt = blockDim.x;
+    const int64_t word = (int64_t)blockIdx.x * nt + threadIdx.x;
     const int64_t j0 = (int64_t)blockIdx.y * rpc;
     const int64_t j1 = min(m, j0 + (int64_t)rpc);
     const bool active = word < nwords;
     const int64_t wstride = stride >> 2;
     const uint32_t* base = reinterpret_cast<const uint32_t*>(packed) + (active ? word : 0);
-    float acc[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) acc[k] = 0.f;
-    // per-SNP table rows of a batch: thread t holds floats 2t, 2t+1 (row t/2)
-    auto fetch_rows = [&](int64_t jb, int nrows) -> float2 {
-        const int r = threadIdx.x >> 1;
-        return r < nrows ? *reinterpret_cast<const float2*>(lut + jb * 4 + 2 * threadIdx.x) : make_float2(0.f, 0.f);
+
+    // the table of pair p of the batch at row jb (rows jb + 2p, jb + 2p + 1) is
+    // built by thread p from the two rows' 4-entry tables: one L2 round trip
+    auto build = [&](int64_t jb, uint32_t tb) {
+        const int p = threadIdx.x;
+        if (p >= kPairBatch) return;
+        const int64_t ra = jb + 2 * p, rb = ra + 1;
+        const float4 la = ra < j1 ? __ldg(reinterpret_cast<const float4*>(lut) + ra) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 lb = rb < j1 ? __ldg(reinterpret_cast<const float4*>(lut) + rb) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4* dst = reinterpret_cast<float4*>(reinterpret_cast<char*>(tabs) + (tb - tabs_sh) + 64u * (uint32_t)p);
+        dst[0] = make_float4(la.x + lb.x, la.y + lb.x, la.z + lb.x, la.w + lb.x);  // c_b = 0
+        dst[1] = make_float4(la.x + lb.y, la.y + lb.y, la.z + lb.y, la.w + lb.y);  // c_b = 1
+        dst[2] = make_float4(la.x + lb.z, la.y + lb.z, la.z + lb.z, la.w + lb.z);  // c_b = 2
+        dst[3] = make_float4(la.x + lb.w, la.y + lb.w, la.z + lb.w, la.w + lb.w);  // c_b = 3
     };
-    auto load_group = [&](int64_t jb, int nrows, int p0, uint32_t (&xa)[4], uint32_t (&xb)[4]) {
-        const uint32_t* rp = base + (jb + 2 * p0) * wstride;
+    // code words of rows r0 .. r0+7; rows past the chunk read its last row (their tables are zero)
+    auto load_group = [&](int64_t r0, uint32_t (&w)[8]) {
+        if (r0 + 8 <= j1) {
+            const uint32_t* rp = base + r0 * wstride;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int ra = 2 * (p0 + q), rb = ra + 1;
-            xa[q] = (ra < nrows) ? __ldg(rp + (2 * q) * wstride) : 0xFFFFFFFFu;
-            xb[q] = (rb < nrows) ? __ldg(rp + (2 * q + 1) * wstride) : 0xFFFFFFFFu;
+            for (int k = 0; k < 8; ++k) w[k] = __ldg(rp + k * wstride);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) w[k] = __ldg(base + min(r0 + k, j1 - 1) * wstride);
         }
     };
-    // The next batch's table rows and first group of code words are fetched
-    // before the current batch is consumed, so the barriers that rebuild the
-    // pair tables do not drain the memory pipeline.
-    uint32_t wa[4], wb[4], na[4], nb[4];
-    int64_t jb = j0;
-    int nrows = (int)min((int64_t)(2 * kPairBatch), j1 - jb);
-    float2 lcur = fetch_rows(jb, nrows);
-    if (active && nrows > 0) load_group(jb, nrows, 0, wa, wb);
-    while (jb < j1) {
-        const int npairs = (nrows + 1) >> 1;
-        __syncthreads();
-        *reinterpret_cast<float2*>(lrow + 2 * threadIdx.x) = lcur;
-        __syncthreads();
-        for (int e = threadIdx.x; e < npairs * 16; e += kThreads) {
-            const int p = e >> 4, ca = e & 3, cb = (e >> 2) & 3;
-            const int ra = 2 * p, rb = 2 * p + 1;
-            tab[e] = lrow[ra * 4 + ca] + (rb < nrows ? lrow[rb * 4 + cb] : 0.f);
-        }
-        __syncthreads();
-        const int64_t jn = jb + 2 * kPairBatch;
-        const int nrn = jn < j1 ? (int)min((int64_t)(2 * kPairBatch), j1 - jn) : 0;
-        if (nrn > 0) lcur = fetch_rows(jn, nrn);
+
+    float2 acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = make_float2(0.f, 0.f);
+    const int nbatch = (int)((j1 - j0 + kPairRows - 1) / kPairRows);
+    build(j0, tb0);
+    __syncthreads();
+    uint32_t w[8];
+    if (active) load_group(j0, w);
+    for (int i = 0; i < nbatch; ++i) {
+        const int64_t jb = j0 + (int64_t)i * kPairRows;
+        const uint32_t tb = tb0 + (uint32_t)(i & 1) * (kPairTab * 4);
+        if (i + 1 < nbatch) build(jb + kPairRows, tb0 + (uint32_t)((i + 1) & 1) * (kPairTab * 4));
         if (active) {
-            for (int p0 = 0; p0 < npairs; p0 += 4) {
-                if (p0 + 4 < npairs) load_group(jb, nrows, p0 + 4, na, nb);
-                else if (nrn > 0) load_group(jn, nrn, 0, na, nb);
+            const int ng = (int)min((int64_t)(kPairRows / 8), (j1 - jb + 7) / 8);
+            for (int g = 0; g < ng; ++g) {
+                uint32_t nw[8];
+                const bool more = g + 1 < ng || i + 1 < nbatch;
+                if (more) load_group(g + 1 < ng ? jb + 8 * (g + 1) : jb + kPairRows, nw);
+                const uint32_t gb = tb + 256u * (uint32_t)g;
+                pair_lookups<0>(w[0], w[1], gb, acc);
+                pair_lookups<1>(w[2], w[3], gb, acc);
+                pair_lookups<2>(w[4], w[5], gb, acc);
+                pair_lookups<3>(w[6], w[7], gb, acc);
+                if (more) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (p0 + q >= npairs) break;
-                    const char* T = reinterpret_cast<const char*>(tab + (p0 + q) * 16);
-                    const uint32_t e = (wa[q] & 0x33333333u) | ((wb[q] & 0x33333333u) << 2);
-                    const uint32_t o = ((wa[q] >> 2) & 0x33333333u) | (wb[q] & 0xCCCCCCCCu);
-                    // byte offsets 4 * index: bytes of eL hold nibbles 0, 2, 4, 6 of e (samples
-                    // 0, 4, 8, 12), bytes of eH nibbles 1, 3, 5, 7 (samples 2, 6, 10, 14); likewise
-                    // for o (odd samples).  One byte-permute then yields each offset.
-                    const uint32_t eL = (e << 2) & 0x3C3C3C3Cu, eH = (e >> 2) & 0x3C3C3C3Cu;
-                    const uint32_t oL = (o << 2) & 0x3C3C3C3Cu, oH = (o >> 2) & 0x3C3C3C3Cu;
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        const uint32_t sel = 0x4440u | (uint32_t)b;
-                        acc[4 * b] += *reinterpret_cast<const float*>(T + __byte_perm(eL, 0u, sel));
-                        acc[4 * b + 1] += *reinterpret_cast<const float*>(T + __byte_perm(oL, 0u, sel));
-                        acc[4 * b + 2] += *reinterpret_cast<const float*>(T + __byte_perm(eH, 0u, sel));
-                        acc[4 * b + 3] += *reinterpret_cast<const float*>(T + __byte_perm(oH, 0u, sel));
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    wa[q] = na[q];
-                    wb[q] = nb[q];
+                    for (int k = 0; k < 8; ++k) w[k] = nw[k];
                 }
             }
         }
-        jb = jn;
-        nrows = nrn;
+        __syncthreads();
     }
     if (!active) return;
     float4* out = reinterpret_cast<float4*>(part + (int64_t)blockIdx.y * ldp + word * 16);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) out[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+    for (int k = 0; k < 4; ++k) out[k] = make_float4(acc[2 * k].x, acc[2 * k].y, acc[2 * k + 1].x, acc[2 * k + 1].y);
 }
 
 __device__ inline double block_sum_to(double v, double* partials_slot) {
@@ -346,19 +395,26 @@ template <typename T>
 cudaError_t launch_matvec(const gkl_handle* h, const T* v, T* y, void* scratch, const Sv* sv, const FinArgs* fa,
                           cudaEvent_t ev0, cudaEvent_t ev1, int* nlaunch) {
     MvPlan p = plan_products(h);
+    constexpr bool fp32 = sizeof(T) == sizeof(float);
+    const int chunks = p.mv_chunks(fp32);
     T* part = static_cast<T*>(scratch);
-    T* lut = part + (size_t)p.chunks * (size_t)p.ldp;
+    T* lut = part + (size_t)chunks * (size_t)p.ldp;
     cudaStream_t st = h->stream;
     k_mv_table<T><<<(unsigned)((h->m + 255) / 256), 256, 0, st>>>(h->m, h->mu, h->d, h->w, v, lut);
-    dim3 grid((unsigned)p.tiles, (unsigned)p.chunks);
     if (ev0) cudaEventRecord(ev0, st);
-    if constexpr (sizeof(T) == sizeof(float))
-        k_mv_pair<<<grid, kThreads, 0, st>>>(h->packed, h->stride, p.nwords, h->m, p.rows_per_chunk,
-                                             reinterpret_cast<const float*>(lut), reinterpret_cast<float*>(part),
-                                             p.ldp);
-    else
-        k_mv_part<T><<<grid, kThreads, 0, st>>>(h->packed, h->stride, p.nwords, h->m, p.rows_per_chunk, lut, part,
-                                                p.ldp);
+    if constexpr (fp32) {
+        // up to eight blocks of 16.6 KB tables on one SM
+        static std::once_flag carveout;
+        std::call_once(carveout, [] {
+            cudaFuncSetAttribute(k_mv_pair, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+        });
+        k_mv_pair<<<dim3((unsigned)p.pair_tiles, (unsigned)p.pair_chunks), p.pair_threads, 0, st>>>(
+            h->packed, h->stride, p.nwords, h->m, p.pair_rpc, reinterpret_cast<const float*>(lut),
+            reinterpret_cast<float*>(part), p.ldp);
+    } else
+        k_mv_part<T><<<dim3((unsigned)p.tiles, (unsigned)p.chunks), kThreads, 0, st>>>(
+            h->packed, h->stride, p.nwords, h->m, p.rows_per_chunk, lut, part, p.ldp);
     if (ev1) cudaEventRecord(ev1, st);
     if (nlaunch) *nlaunch = 3;
     FinArgs f{};
@@ -367,7 +423,7 @@ cudaError_t launch_matvec(const gkl_handle* h, const T* v, T* y, void* scratch, 
     if (sv) s = *sv;
     // 32 outputs per block pass; at most 4 blocks per SM (the partial-norm buffer's size)
     const int fblocks = (int)std::min<int64_t>((h->n + 31) / 32, 4 * (int64_t)h->num_sms);
-    k_mv_fin<T><<<(unsigned)std::max(1, fblocks), 256, 0, st>>>(part, p.ldp, p.chunks, h->n, h->s, y, f, s);
+    k_mv_fin<T><<<(unsigned)std::max(1, fblocks), 256, 0, st>>>(part, p.ldp, chunks, h->n, h->s, y, f, s);
     return cudaGetLastError();
 }
 
