@@ -272,10 +272,11 @@ def run_ours(args):
     rmv_ms = sum(i["ms_rmv"] for i in infos) / max(1, sum(i["n_rmv"] for i in infos))
     tot_mv = sum(i["ms_mv"] for i in infos)
     tot_rmv = sum(i["ms_rmv"] for i in infos)
-    # the FP32 path runs k_mv_pair (packed_ops.cu) and k_rmv_tc (packed_tc.cu; k_rmv_mma in
-    # packed_mma.cu with GKL_RMV_KERNEL=mma); algorithmic bytes per launch = packed G once + the
-    # FP32 input and output vectors
-    rk = ("k_rmv_mma", "packed_mma.cu") if os.environ.get("GKL_RMV_KERNEL") == "mma" else ("k_rmv_tc", "packed_tc.cu")
+    # the FP32 path runs k_mv_pair (packed_ops.cu) and k_rmv_tc (packed_tc.cu; k_rmv_n256 with
+    # GKL_RMV_KERNEL=n256, k_rmv_mma in packed_mma.cu with GKL_RMV_KERNEL=mma); algorithmic bytes
+    # per launch = packed G once + the FP32 input and output vectors
+    rk = {"mma": ("k_rmv_mma", "packed_mma.cu"), "n256": ("k_rmv_n256", "packed_tc.cu")}.get(
+        os.environ.get("GKL_RMV_KERNEL", ""), ("k_rmv_tc", "packed_tc.cu"))
     mv = ("k_mv_pair", "packed_ops.cu", mv_ms, packed_bytes + 4 * m + 4 * n)
     rmv = (rk[0], rk[1], rmv_ms, packed_bytes + 4 * n + 4 * m)
     dom, oth = (mv, rmv) if tot_mv >= tot_rmv else (rmv, mv)

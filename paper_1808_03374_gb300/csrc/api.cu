@@ -564,9 +564,11 @@ int gkl_init(gkl_handle** out, const uint8_t* packed, int64_t n, int64_t m, int6
         gkl_destroy(h);
         return GKL_ERR_CUDA;
     }
-    // FP32 A^T u runs on the tcgen05 kernel; GKL_RMV_KERNEL=mma selects the
-    // mma.sync kernel instead (kept for comparison)
+    // FP32 A^T u runs on the N = 16 tcgen05 kernel; GKL_RMV_KERNEL=n256 selects
+    // the tcgen05 kernel with the codes on the N side and GKL_RMV_KERNEL=mma the
+    // mma.sync kernel (both kept for comparison)
     const char* rk = std::getenv("GKL_RMV_KERNEL");
+    h->rmv_n256 = rk && std::strcmp(rk, "n256") == 0;
     if (rk && std::strcmp(rk, "mma") == 0)
         h->tc_state = -1;
     else

@@ -101,6 +101,7 @@ struct gkl_handle {
     size_t gws_bytes;
     // tensor-core (tcgen05) A^T u: 0 = not prepared, 1 = ready, -1 = unavailable or disabled
     int tc_state;
+    int rmv_n256;  // 1: the N = 256 tensor-core kernel (k_rmv_n256) instead of the N = 16 one (k_rmv_tc)
     alignas(64) unsigned char tc_map[128];  // TMA descriptor of the packed matrix
     int64_t* miss_off;   // CSR of the missing codes per SNP (m + 1 offsets), built by tc_prepare
     uint32_t* miss_idx;  // sample indices, ascending per SNP

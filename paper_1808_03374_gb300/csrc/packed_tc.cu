@@ -52,6 +52,7 @@
 
 #include "epilogue.cuh"
 #include "gkl_internal.cuh"
+#include "tc_layout.cuh"
 #include "tc_ptx.cuh"
 
 namespace gkl {
@@ -483,12 +484,13 @@ __global__ void __launch_bounds__(256) k_miss_fill(const uint8_t* __restrict__ p
 // j, four SNPs per warp, eight list entries in flight per lane (the kernel is
 // bound by memory latency times the number of warp waves).  Z_a, Z_b = sums of
 // z_i over the listed samples of class a (i even) and b (i odd), exact in 64-bit
-// integers; p1[j] -= S 2^-28 (3 Z_a + 4 Z_b), p3[j] += S 2^-28 (Z_a + Z_b)
-// (range-0 partials).
+// integers; p3[j] += S 2^-28 (Z_a + Z_b) and, for the operand of k_rmv_tc
+// (affine in the code, so a missing code contributes 3/8 or 3/4 of z_i),
+// p1[j] -= S 2^-28 (3 Z_a + 4 Z_b) (range-0 partials).
 __global__ void __launch_bounds__(256) k_miss_gather(const int64_t* __restrict__ off, const uint32_t* __restrict__ idx,
                                                       int64_t m, const int* __restrict__ z,
                                                       const double* __restrict__ dsc, double* __restrict__ p1,
-                                                      double* __restrict__ p3) {
+                                                      double* __restrict__ p3, int affine) {
     const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
     const int sl = threadIdx.x & 7;
     long long za = 0, zb = 0;
@@ -516,8 +518,301 @@ __global__ void __launch_bounds__(256) k_miss_gather(const int64_t* __restrict__
     }
     if (j < m && sl == 0 && (za | zb)) {
         const double zs = ldexp(dsc[0], -28);
-        p1[j] -= zs * (double)(3 * za + 4 * zb);
+        if (affine) p1[j] -= zs * (double)(3 * za + 4 * zb);
         p3[j] += zs * (double)(za + zb);
+    }
+}
+
+// ---- A^T u with the codes on the N side ----------------------------------------
+//
+// The same product in the orientation of the block products: M = 128 rows of
+// which rows 0-6 hold the seven base-16 digits of u~ (the other rows of the
+// digit tiles stay zero), N = 256 SNPs whose codes are decoded by byte permutes
+// into f(code) = g [observed] = 0, 1, 2, 0 in shared memory (128-byte swizzle,
+// K-major), K = samples.  One MMA covers 256 x 32 codes, twice the codes of the
+// N = 16 orientation above at about the same cost per instruction, but it moves
+// 24 KB of shared memory per MMA (the decoded operand written and read, the
+// digit tile read), against 0.5 KB for the N = 16 kernel: measured 116 us per
+// launch at 10,000 x 100,000 against 110 us, so the N = 16 kernel stays the
+// default (GKL_RMV_KERNEL=n256 selects this one).  The digits
+// are those of u~'_i = S 2^-28 X_i, X_i = rint(u~_i 2^28 / S); every
+// accumulator value F_p,j = sum_i f(c_ij) delta_p,i is an exact integer in
+// FP32 (|F_p| <= 32 x 512 x 1023 < 2^24 for K-ranges of at most 1023 stages),
+// and the epilogue recombines z1_j = sum_p 16^(6-p) F_p,j = sum_{i obs} g_ij X_i
+// in 64-bit integers.  Partials: p1[r][j] = S 2^-28 z1_j, p3[r][j] = 0; the
+// missing-code gather adds S 2^-28 sum_{i missing} X_i to p3[0][j] and the
+// finishing kernel forms d_j w_j (sum_r p1 - mu_j (sum_i u~_i - sum_r p3)).
+//
+// Warp roles: 0 copies (two 128-row TMA boxes and four 1 KB digit images per
+// 512-sample stage), 1 issues the MMAs, 2-3 and 5-10 decode (one SNP row per
+// lane), 4 runs the epilogue (tensor-memory lanes 0-31 hold digit rows 0-31).
+namespace {
+constexpr int kN2Rows = 256;                         // SNPs per tile (MMA N)
+constexpr int kN2Box = 2 * kPackedBytes;             // 32 KB: two 128-row boxes of one stage
+constexpr int kN2Tile = 16384;                       // one digit tile: 128 rows x 128 bytes
+constexpr int kN2Img = 1024;                         // rows 0-7 of a digit tile (one 128-sample sub-stage)
+constexpr int kN2RP = 3, kN2RG = 4, kN2RD = 2;       // ring depths: packed stages, digit tiles, decoded tiles
+constexpr int kN2DecWarps = 8;
+constexpr int kN2Threads = 32 * (2 + kN2DecWarps + 1);  // 352
+constexpr int kN2EpiWarp = 4;
+constexpr int kN2MaxRangeStages = 1023;              // 523,776 samples: |F_p| < 2^24
+constexpr uint32_t kN2Lut = 0x00403800u;             // e4m3 bytes of f: 0, 1, 2, 0
+constexpr uint32_t kN2Idesc = tc::idesc_e4m3(256, 0);
+constexpr int kN2Smem = 1024 + kN2RP * kN2Box + kN2RG * kN2Tile + kN2RD * 2 * kN2Tile + 1024;
+static_assert(kN2Smem <= 232448, "shared memory of k_rmv_n256");
+}  // namespace
+
+// One block per 128-sample sub-stage: the 1 KB image of digit rows 0-7 (row 7
+// zero) in the swizzled K order of the decode, and X_i into z[] (i < n).
+__global__ void __launch_bounds__(128) k_n2_digits(const float* __restrict__ u, const float* __restrict__ s,
+                                                   int64_t n, const double* __restrict__ dsc,
+                                                   uint8_t* __restrict__ img, int* __restrict__ z) {
+    const int g = blockIdx.x, loc = threadIdx.x;
+    const int64_t i = (int64_t)g * 128 + loc;
+    long long X = 0;
+    if (i < n) X = llrint((double)u[i] * (s ? (double)s[i] : 1.0) * dsc[1] * 268435456.0);  // |X| <= 2^28
+    if (i < n) z[i] = (int)X;
+    int dg[8];
+    dg[7] = 0;
+    for (int p = 6; p >= 1; --p) {
+        const int r = (int)((X + 8) & 15) - 8;
+        dg[p] = r;
+        X = (X - r) >> 4;
+    }
+    dg[0] = (int)X;  // in [-16, 16]
+    const int kk = 16 * (loc >> 4) + bt_kpos(loc & 15);
+    uint8_t* t = img + (size_t)g * kN2Img;
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+        t[bt_swz(p, kk)] = (uint8_t)__nv_cvt_float_to_fp8((float)dg[p], __NV_SATFINITE, __NV_E4M3);
+}
+
+struct N2Args {
+    const uint8_t* img;  // 4 * nstages digit images
+    int nstages, range_stages, nranges, ntiles;
+    int64_t m;
+    const double* dsc;
+    double* p1;
+    double* p3;
+    int* err;
+};
+
+__global__ void __launch_bounds__(kN2Threads, 1) k_rmv_n256(const __grid_constant__ CUtensorMap tmap, N2Args a) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = sm_addr(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* sb = smem_raw + (base - raw);
+    const uint32_t sP = base, sG = sP + kN2RP * kN2Box, sD = sG + kN2RG * kN2Tile;
+    const uint32_t sBar = sD + kN2RD * 2 * kN2Tile;
+    uint8_t* gP = sb;
+    uint8_t* gG = sb + kN2RP * kN2Box;
+    uint8_t* gD = gG + kN2RG * kN2Tile;
+    auto pfull = [&](int i) { return sBar + 8u * i; };
+    auto pempty = [&](int i) { return sBar + 8u * (kN2RP + i); };
+    auto gfull = [&](int i) { return sBar + 8u * (2 * kN2RP + i); };
+    auto gempty = [&](int i) { return sBar + 8u * (2 * kN2RP + kN2RG + i); };
+    auto dfull = [&](int i) { return sBar + 8u * (2 * kN2RP + 2 * kN2RG + i); };
+    auto dempty = [&](int i) { return sBar + 8u * (2 * kN2RP + 2 * kN2RG + kN2RD + i); };
+    auto afull = [&](int i) { return sBar + 8u * (2 * kN2RP + 2 * kN2RG + 2 * kN2RD + i); };
+    auto aempty = [&](int i) { return sBar + 8u * (2 * kN2RP + 2 * kN2RG + 2 * kN2RD + 2 + i); };
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sb + (sBar - base) + 512);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // digit rows 8-127 of every ring tile stay zero; the copies write rows 0-7
+    for (int o = 16 * threadIdx.x; o < kN2RG * kN2Tile; o += 16 * kN2Threads)
+        *reinterpret_cast<uint4*>(gG + o) = make_uint4(0u, 0u, 0u, 0u);
+    tc::fence_proxy_async();
+    if (warp == 0) tc::tmem_alloc(sm_addr(tmem_slot), 512);
+    if (threadIdx.x == 32) {
+        for (int i = 0; i < kN2RP; ++i) {
+            bar_init(pfull(i), 1);
+            bar_init(pempty(i), kN2DecWarps);
+        }
+        for (int i = 0; i < kN2RG; ++i) {
+            bar_init(gfull(i), 1);
+            bar_init(gempty(i), 1);
+        }
+        for (int i = 0; i < kN2RD; ++i) {
+            bar_init(dfull(i), kN2DecWarps);
+            bar_init(dempty(i), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            bar_init(afull(i), 1);
+            bar_init(aempty(i), 1);
+        }
+        tc::bar_init_fence();
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int nitems = a.ntiles * a.nranges;
+    auto fail = [&](int code) { atomicCAS(a.err, 0, code); };
+    auto stages_of = [&](int item, int& k0, int& k1) {
+        const int r = item % a.nranges;
+        k0 = r * a.range_stages;
+        k1 = min(a.nstages, k0 + a.range_stages);
+    };
+
+    if (warp == 0) {
+        // ---- copies: per stage two packed boxes, then its four digit images
+        if (lane == 0) {
+            uint32_t ps = 0, gs = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+                const int tile = item / a.nranges;
+                int k0, k1;
+                stages_of(item, k0, k1);
+                for (int k = k0; k < k1 && ok; ++k, ++ps) {
+                    const int sp = (int)(ps % kN2RP);
+                    if (!bar_wait(pempty(sp), ((ps / kN2RP) & 1u) ^ 1u)) {
+                        fail(41);
+                        ok = false;
+                        break;
+                    }
+                    bar_expect_tx(pfull(sp), kN2Box);
+                    tma_2d(sP + sp * kN2Box, &tmap, kStageRowBytes * k, kN2Rows * tile, pfull(sp));
+                    tma_2d(sP + sp * kN2Box + kPackedBytes, &tmap, kStageRowBytes * k, kN2Rows * tile + kRows,
+                           pfull(sp));
+                    for (int qq = 0; qq < 4; ++qq, ++gs) {
+                        const int sg = (int)(gs % kN2RG);
+                        if (!bar_wait(gempty(sg), ((gs / kN2RG) & 1u) ^ 1u)) {
+                            fail(42);
+                            ok = false;
+                            break;
+                        }
+                        bar_expect_tx(gfull(sg), kN2Img);
+                        bulk_g2s(sG + sg * kN2Tile, a.img + (size_t)(4 * k + qq) * kN2Img, kN2Img, gfull(sg));
+                    }
+                }
+            }
+            // drain: every issued copy has landed before the CTA may exit
+            for (uint32_t x = ps > (uint32_t)kN2RP ? ps - kN2RP : 0u; x < ps; ++x)
+                if (!bar_wait(pfull((int)(x % kN2RP)), (x / kN2RP) & 1u)) fail(43);
+            for (uint32_t x = gs > (uint32_t)kN2RG ? gs - kN2RG : 0u; x < gs; ++x)
+                if (!bar_wait(gfull((int)(x % kN2RG)), (x / kN2RG) & 1u)) fail(44);
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer: per 128-sample sub-stage four K-steps of 32 samples
+        if (lane == 0) {
+            uint32_t it = 0, li = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
+                int k0, k1;
+                stages_of(item, k0, k1);
+                const int nsub = 4 * (k1 - k0);
+                const uint32_t acc = li & 1u;
+                if (!bar_wait(aempty(acc), ((li >> 1) & 1u) ^ 1u)) {
+                    fail(45);
+                    break;
+                }
+                tc::fence_after();
+                const uint32_t dcol = tmem + 256u * acc;
+                for (int g = 0; g < nsub; ++g, ++it) {
+                    const int sg = (int)(it % kN2RG), sd = (int)(it % kN2RD);
+                    if (!bar_wait(gfull(sg), (it / kN2RG) & 1u) || !bar_wait(dfull(sd), (it / kN2RD) & 1u)) {
+                        fail(46);
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after();
+                    const uint64_t ad = desc_sw128(sG + sg * kN2Tile);
+                    const uint64_t bd = desc_sw128(sD + sd * 2 * kN2Tile);
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) tc::mma_f8_ss(dcol, ad + 2 * ks, bd + 2 * ks, kN2Idesc, (g | ks) != 0);
+                    mma_commit(gempty(sg));
+                    mma_commit(dempty(sd));
+                }
+                if (ok) mma_commit(afull(acc));
+            }
+            if (it > 0) {  // the last commit covers every MMA issued
+                const uint32_t x = it - 1;
+                if (!bar_wait(dempty((int)(x % kN2RD)), (x / kN2RD) & 1u)) fail(47);
+            }
+        }
+    } else if (warp == kN2EpiWarp) {
+        // ---- epilogue: lane p < 7 holds digit row p; 16 x 16 accumulator columns per item
+        const int p = lane & 7;
+        const int sh = lane < 7 ? 4 * (6 - lane) : 0;
+        const double zs = ldexp(a.dsc[0], -28);
+        uint32_t li = 0;
+        for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++li) {
+            const int tile = item / a.nranges, range = item % a.nranges;
+            const uint32_t acc = li & 1u;
+            if (!bar_wait(afull(acc), (li >> 1) & 1u)) {
+                fail(48);
+                break;
+            }
+            tc::fence_after();
+#pragma unroll 1
+            for (int g = 0; g < 16; ++g) {
+                long long zv[16];
+                bt_ld16_scaled(tmem + 256u * acc + 16u * g, sh, zv);
+                if (g == 15) {
+                    tc::fence_before();
+                    __syncwarp();
+                    if (lane == 0) bar_arrive(aempty(acc));
+                }
+                bt_reduce_scatter<8>(zv, p);
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int64_t j = (int64_t)tile * kN2Rows + 16 * g + 2 * p + i;
+                    if (lane < 8 && j < a.m) {
+                        a.p1[(int64_t)range * a.m + j] = zs * (double)zv[i];
+                        a.p3[(int64_t)range * a.m + j] = 0.0;
+                    }
+                }
+            }
+        }
+    } else {
+        // ---- decode: SNP row 32 dw + lane of the tile, one 128-sample sub-stage at a time
+        const int dw = warp < kN2EpiWarp ? warp - 2 : warp - 3;
+        const int row = 32 * dw + lane, box = row >> 7, r7 = row & 7;
+        uint32_t ps = 0, it = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            int k0, k1;
+            stages_of(item, k0, k1);
+            for (int k = k0; k < k1 && ok; ++k, ++ps) {
+                const int sp = (int)(ps % kN2RP);
+                if (!bar_wait(pfull(sp), (ps / kN2RP) & 1u)) {
+                    fail(49);
+                    ok = false;
+                    break;
+                }
+                const uint8_t* src = gP + sp * kN2Box + box * kPackedBytes + (row & 127) * kStageRowBytes;
+                for (int qq = 0; qq < 4; ++qq, ++it) {
+                    const int sd = (int)(it % kN2RD);
+                    const uint4 P0 = *reinterpret_cast<const uint4*>(src + (((2 * qq) ^ r7) << 4));
+                    const uint4 P1 = *reinterpret_cast<const uint4*>(src + (((2 * qq + 1) ^ r7) << 4));
+                    if (!bar_wait(dempty(sd), ((it / kN2RD) & 1u) ^ 1u)) {
+                        fail(50);
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* t = gD + sd * 2 * kN2Tile + (row >> 3) * 1024 + r7 * 128;
+                    const uint32_t Wv[8] = {P0.x, P0.y, P0.z, P0.w, P1.x, P1.y, P1.z, P1.w};
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const uint32_t s0 = Wv[u] & 0x33333333u, s1 = (Wv[u] >> 2) & 0x33333333u;
+                        *reinterpret_cast<uint4*>(t + ((u ^ r7) << 4)) =
+                            make_uint4(__byte_perm(kN2Lut, 0, s0), __byte_perm(kN2Lut, 0, s0 >> 16),
+                                       __byte_perm(kN2Lut, 0, s1), __byte_perm(kN2Lut, 0, s1 >> 16));
+                    }
+                    tc::fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) bar_arrive(dfull(sd));
+                }
+                __syncwarp();
+                if (ok && lane == 0) bar_arrive(pempty(sp));
+            }
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, 512);
     }
 }
 
@@ -558,10 +853,47 @@ static TcPlan plan_tc(const gkl_handle* h) {
     return p;
 }
 
+struct N2Plan {
+    int nstages, range_stages, nranges, ntiles, grid;
+    size_t img_bytes, z_bytes, part_bytes;
+};
+
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Work items (256-SNP tile, K-range) of k_rmv_n256: K-ranges of at most 1023
+// stages; more ranges only where they even out the last wave over the SMs.
+static N2Plan plan_n2(const gkl_handle* h) {
+    N2Plan p;
+    p.nstages = (int)((h->stride + kStageRowBytes - 1) / kStageRowBytes);
+    p.ntiles = (int)((h->m + kN2Rows - 1) / kN2Rows);
+    const int sms = std::max(1, h->num_sms);
+    const int nr0 = (p.nstages + kN2MaxRangeStages - 1) / kN2MaxRangeStages;
+    int best = nr0;
+    double best_eff = 0.0;
+    for (int nr = nr0; nr <= std::min(p.nstages, nr0 + 7); ++nr) {
+        const int rs = (p.nstages + nr - 1) / nr, nranges = (p.nstages + rs - 1) / rs;
+        const double items = (double)p.ntiles * nranges;
+        const double eff = items / (std::ceil(items / sms) * sms);
+        if (eff > best_eff + 0.03) {
+            best_eff = eff;
+            best = nr;
+        }
+    }
+    p.range_stages = (p.nstages + best - 1) / best;
+    p.nranges = (p.nstages + p.range_stages - 1) / p.range_stages;
+    p.grid = (int)std::min<int64_t>((int64_t)p.ntiles * p.nranges, sms);
+    p.img_bytes = (size_t)p.nstages * 4 * kN2Img;
+    p.z_bytes = (size_t)p.nstages * kStageSamples * sizeof(int);
+    p.part_bytes = 2 * (size_t)p.nranges * (size_t)h->m * sizeof(double);
+    return p;
+}
+
 size_t rmv_tc_scratch_bytes(const gkl_handle* h) {
     const TcPlan p = plan_tc(h);
-    return p.dig_bytes + ((p.cs_bytes + 255) & ~(size_t)255) + ((p.z_bytes + 255) & ~(size_t)255) + p.part_bytes +
-           256;
+    const N2Plan q = plan_n2(h);
+    const size_t n16 = p.dig_bytes + al256(p.cs_bytes) + al256(p.z_bytes) + p.part_bytes + 256;
+    const size_t n256 = al256(q.img_bytes) + al256(q.z_bytes) + q.part_bytes + 256;
+    return std::max(n16, n256);
 }
 
 // Prepares the tensor-core path for a handle: the TMA descriptor of the packed
@@ -590,7 +922,8 @@ bool tc_prepare(gkl_handle* h) {
     if (r != CUDA_SUCCESS) return false;
     static_assert(sizeof(CUtensorMap) == sizeof(h->tc_map), "tensor map size");
     memcpy(h->tc_map, &map, sizeof(map));
-    if (cudaFuncSetAttribute(k_rmv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_rmv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess ||
+        cudaFuncSetAttribute(k_rmv_n256, cudaFuncAttributeMaxDynamicSharedMemorySize, kN2Smem) != cudaSuccess)
         return false;
     // list of missing codes per SNP (CSR), built once: counts, host prefix sum, fill
     const int64_t m = h->m;
@@ -621,8 +954,45 @@ bool tc_prepare(gkl_handle* h) {
     return true;
 }
 
+// N = 256 orientation: scale pass, digit images, the MMA kernel, the missing-code
+// gather (p3 only) and the finishing kernel.
+static cudaError_t launch_rmatvec_n256(const gkl_handle* h, const float* u, float* x, void* scratch, const Sv* sv,
+                                       const FinArgs* fa, cudaEvent_t ev0, cudaEvent_t ev1, int* nlaunch) {
+    const N2Plan p = plan_n2(h);
+    uint8_t* img = static_cast<uint8_t*>(scratch);
+    int* z = reinterpret_cast<int*>(img + al256(p.img_bytes));
+    double* p1 = reinterpret_cast<double*>(reinterpret_cast<char*>(z) + al256(p.z_bytes));
+    double* p3 = p1 + (size_t)p.nranges * h->m;
+    double* aux = h->aux;
+    double* dsc = aux;
+    unsigned* counter = reinterpret_cast<unsigned*>(aux + 4);
+    double* part = aux + 8;
+    int* err = reinterpret_cast<int*>(reinterpret_cast<char*>(aux) + kAuxErrOffset);
+    cudaStream_t st = h->stream;
+    const int sblocks = std::min(2 * h->num_sms, (int)((h->n + 255) / 256));
+    k_u_scale<<<std::max(1, sblocks), 256, 0, st>>>(u, h->s, h->n, part, counter, dsc);
+    k_n2_digits<<<4 * p.nstages, 128, 0, st>>>(u, h->s, h->n, dsc, img, z);
+    alignas(64) CUtensorMap map;
+    memcpy(&map, h->tc_map, sizeof(map));
+    N2Args a{img, p.nstages, p.range_stages, p.nranges, p.ntiles, h->m, dsc, p1, p3, err};
+    if (ev0) cudaEventRecord(ev0, st);
+    k_rmv_n256<<<p.grid, kN2Threads, kN2Smem, st>>>(map, a);
+    if (ev1) cudaEventRecord(ev1, st);
+    k_miss_gather<<<(unsigned)((h->m * 8 + 255) / 256), 256, 0, st>>>(h->miss_off, h->miss_idx, h->m, z, dsc, p1,
+                                                                       p3, 0);
+    FinArgs f{};
+    Sv s{};
+    if (fa) f = *fa;
+    if (sv) s = *sv;
+    k_rmv_mma_fin<<<(unsigned)((h->m + 255) / 256), 256, 0, st>>>(p1, p3, p.nranges, h->m, h->mu, h->d, h->w, dsc, x,
+                                                                    f, s);
+    if (nlaunch) *nlaunch = 5;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_rmatvec_tc(const gkl_handle* h, const float* u, float* x, void* scratch, const Sv* sv,
                               const FinArgs* fa, cudaEvent_t ev0, cudaEvent_t ev1, int* nlaunch) {
+    if (h->rmv_n256) return launch_rmatvec_n256(h, u, x, scratch, sv, fa, ev0, ev1, nlaunch);
     const TcPlan p = plan_tc(h);
     uint8_t* dig = static_cast<uint8_t*>(scratch);
     int* cs = reinterpret_cast<int*>(dig + p.dig_bytes);
@@ -645,7 +1015,7 @@ cudaError_t launch_rmatvec_tc(const gkl_handle* h, const float* u, float* x, voi
     k_rmv_tc<<<p.grid, kThreads, kSmemBytes, st>>>(map, a);
     if (ev1) cudaEventRecord(ev1, st);
     k_miss_gather<<<(unsigned)((h->m * 8 + 255) / 256), 256, 0, st>>>(h->miss_off, h->miss_idx, h->m, z, dsc, p1,
-                                                                       p3);
+                                                                       p3, 1);
     FinArgs f{};
     Sv s{};
     if (fa) f = *fa;
