@@ -162,6 +162,18 @@ def make_inputs():
     return w, g
 
 
+def cpu_model() -> str:
+    """The host CPU's model name as lscpu reports it ("" if unavailable)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+    except (OSError, subprocess.SubprocessError):
+        return ""
+    for line in out.splitlines():
+        if line.startswith("Model name:"):
+            return line.split(":", 1)[1].strip()
+    return ""
+
+
 def cpu_baseline_sample(w, g, budget_s=15.0, max_pairs=40):
     """The FP64 oracle, as it stands, on a bounded sample of the same workload:
     repeated A.v / A^T.u pairs over the full matrix (the per-step cost of GKL)."""
@@ -181,7 +193,7 @@ def cpu_baseline_sample(w, g, budget_s=15.0, max_pairs=40):
             break
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": pairs / dt, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+    return {"value": pairs / dt, "unit": "pairs/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
             "sample": f"{pairs} A.v + A^T.u pairs of the FP64 CPU oracle on the full {g.n} x {g.m} packed matrix "
                       f"({dt:.1f} s)"}
 
@@ -216,7 +228,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": g.n, "m": g.m, "step": "one A.v + A^T.u pair of the FP64 oracle"},
-            "cpu_baseline": {"value": val, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": val, "unit": "pairs/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
                              "sample": f"{args.steps} oracle pairs on the full matrix"},
             "e2e": {"value": val, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -611,7 +623,7 @@ def run_cpu_table(args):
         line = [x for x in res.stdout.splitlines() if x.startswith("{")]
         rows.append(json.loads(line[-1])["cpu_pairs"] if line else {"workload": name, "threads": threads,
                                                                       "error": res.stderr[-300:]})
-    print(json.dumps({"cpu_table": {"host_cores": cores, "rows": rows}}), flush=True)
+    print(json.dumps({"cpu_table": {"host_cores": cores, "cpu": cpu_model(), "rows": rows}}), flush=True)
     return 0
 
 
