@@ -208,6 +208,12 @@ def run_reference(args):
     import synth
     M = oracle.Matrix.from_packed(g.packed, g.n)
     v = synth.normal_vec(77, 0, g.m)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    if world > 1:
+        # the launcher gives every rank OMP_NUM_THREADS=1; rank 0 alone runs the
+        # oracle here, on all host cores as at one GPU
+        cores = os.cpu_count() or 1
+        ctypes.CDLL("libgomp.so.1").omp_set_num_threads(cores)
 
     def step():
         nonlocal v
@@ -223,7 +229,6 @@ def run_reference(args):
         step()
     dt = time.perf_counter() - t0
     val = args.steps / dt
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "pairs/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
