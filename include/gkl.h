@@ -139,6 +139,10 @@ int gkl_colstats(const uint8_t* packed, int64_t n, int64_t m, int64_t stride,
  *   handle computes them with gkl_colstats.
  * stream: cudaStream_t (as void*) used for all later work; NULL = default.
  * Allocates device memory for its own state (released by gkl_destroy).
+ * The FP32 A^T u kernel is chosen here from the environment: by default the
+ * tcgen05 kernel with N = 16 (k_rmv_tc); GKL_RMV_KERNEL=n256 selects the
+ * tcgen05 kernel with 256 SNPs on the MMA's N side and GKL_RMV_KERNEL=mma the
+ * mma.sync kernel (both for comparison; same results within FP32 rounding).
  * Errors: GKL_ERR_ARG (sizes, alignment, exactly one of mu/scale NULL),
  *   GKL_ERR_CUDA. On error *h is NULL. */
 int gkl_init(gkl_handle** h, const uint8_t* packed, int64_t n, int64_t m, int64_t stride,
