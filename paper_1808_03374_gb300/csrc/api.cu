@@ -48,6 +48,24 @@ int ensure_scratch(gkl_handle* h, size_t bytes) {
     return GKL_OK;
 }
 
+// Synchronise the handle's stream and report (then clear) a bounded
+// tensor-core pipeline wait that ran out since the last check.
+int take_pending_error(gkl_handle* h) {
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_err(h, e, "stream synchronisation");
+    if (!h->aux) return GKL_OK;
+    int terr = 0;
+    int* ew = reinterpret_cast<int*>(reinterpret_cast<char*>(h->aux) + kAuxErrOffset);
+    e = cudaMemcpyAsync(&terr, ew, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_err(h, e, "error-word read");
+    if (terr == 0) return GKL_OK;
+    e = cudaMemsetAsync(ew, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_err(h, e, "error-word clear");
+    return set_err(h, GKL_ERR_CUDA, "tensor-core product: a bounded pipeline wait ran out (code %d)", terr);
+}
+
 static int ensure_ws(gkl_handle* h, size_t bytes) {
     if (h->ws_bytes >= bytes) return GKL_OK;
     if (h->ws) cudaFree(h->ws);
@@ -59,16 +77,39 @@ static int ensure_ws(gkl_handle* h, size_t bytes) {
     return GKL_OK;
 }
 
-static bool is_device_ptr(const void* p) {
+int mem_kind(const void* p, int device) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return MEM_BAD;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)
+        return a.device == device ? MEM_DEVICE : MEM_BAD;
+    return MEM_HOST;  // cudaMemoryTypeHost or cudaMemoryTypeUnregistered
 }
 
+static int current_device() {
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return d;
+}
+
+// Device memory of the current device.
+static bool is_device_ptr(const void* p) { return mem_kind(p, current_device()) == MEM_DEVICE; }
+
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Numerical rank among the k leading values (descending): the count of values
+// above 1000 * eps_w * sigma_1, eps_w the unit roundoff of the arithmetic.
+int numerical_rank(const double* sg, int k, double eps_w) {
+    const double thr = 1e3 * eps_w * (k > 0 ? sg[0] : 0.0);
+    int r = 0;
+    while (r < k && sg[r] > thr) ++r;
+    return r;
+}
 
 // Host copy of the device scalars (read once per cycle).
 struct HostState {
@@ -157,9 +198,17 @@ struct Driver {
     }
 
     int cgs(int mode, T* x, int64_t len, const T* W, int64_t ldw, int ncols, const int* cond, int role, int j,
-            uint32_t draw = 0) {
+            uint32_t draw = 0, int* second = nullptr) {
         ++launches;
-        return check(launch_cgs<T>(sv, h->stream, mode, x, len, W, ldw, ncols, cond, role, j, draw, h->num_sms), "cgs");
+        return check(launch_cgs<T>(sv, h->stream, mode, x, len, W, ldw, ncols, cond, role, j, draw, h->num_sms, second),
+                     "cgs");
+    }
+
+    // Flag and count of the adaptive second Gram-Schmidt pass of one side (DGKS
+    // and ONESIDED), or null where both passes always run (FULL and PARTIAL).
+    int* second_of(int side) {
+        if (sv.reorth != GKL_REORTH_DGKS && sv.reorth != GKL_REORTH_ONESIDED) return nullptr;
+        return side == 0 ? sv.sc->second_u : sv.sc->second_v;
     }
 
     int scale(T* x, int64_t len, const double* f) {
@@ -178,10 +227,11 @@ struct Driver {
         if (st) return st;
         if (j > 0) {
             const int* cond = &sv.sc->reorth_u;
+            int* sec = second_of(0);
             mark(ev_cgs, used_cgs, false);
-            if ((st = cgs(CGS_DOTS, y, n, U, sv.ldu, j, cond, 0, j))) return st;
-            if ((st = cgs(CGS_UPD_DOTS, y, n, U, sv.ldu, j, cond, 0, j))) return st;
-            if ((st = cgs(CGS_UPD_NORM, y, n, U, sv.ldu, j, cond, ROLE_U_POST, j))) return st;
+            if ((st = cgs(CGS_DOTS, y, n, U, sv.ldu, j, cond, 0, j, 0, sec))) return st;
+            if ((st = cgs(CGS_UPD_DOTS, y, n, U, sv.ldu, j, cond, 0, j, 0, sec))) return st;
+            if ((st = cgs(CGS_UPD_NORM, y, n, U, sv.ldu, j, cond, ROLE_U_POST, j, 0, sec))) return st;
             mark(ev_cgs, used_cgs, true);
         }
         return scale(y, n, &sv.sc->scale_u);
@@ -197,10 +247,11 @@ struct Driver {
         launches += nl;
         if (st) return st;
         const int* cond = &sv.sc->reorth_v;
+        int* sec = second_of(1);
         mark(ev_cgs, used_cgs, false);
-        if ((st = cgs(CGS_DOTS, x, m, V, sv.ldv, j + 1, cond, 0, j))) return st;
-        if ((st = cgs(CGS_UPD_DOTS, x, m, V, sv.ldv, j + 1, cond, 0, j))) return st;
-        if ((st = cgs(CGS_UPD_NORM, x, m, V, sv.ldv, j + 1, cond, ROLE_V_POST, j))) return st;
+        if ((st = cgs(CGS_DOTS, x, m, V, sv.ldv, j + 1, cond, 0, j, 0, sec))) return st;
+        if ((st = cgs(CGS_UPD_DOTS, x, m, V, sv.ldv, j + 1, cond, 0, j, 0, sec))) return st;
+        if ((st = cgs(CGS_UPD_NORM, x, m, V, sv.ldv, j + 1, cond, ROLE_V_POST, j, 0, sec))) return st;
         mark(ev_cgs, used_cgs, true);
         return scale(x, m, &sv.sc->scale_v);
     }
@@ -259,12 +310,6 @@ static int run_svd(gkl_handle* h, const gkl_opts* o, double* sigma, T* Uout, T* 
         return set_err(h, GKL_ERR_ARG, "need 1 <= k < ell <= min(n, m, %d) (k=%d ell=%d)", GKL_MAX_ELL, k, ell);
     if (kk < k || kk >= ell) return set_err(h, GKL_ERR_ARG, "need k <= k_keep < ell (k_keep=%d)", kk);
     if (o->maxit < 1 || !(o->tol >= 0.0)) return set_err(h, GKL_ERR_ARG, "need maxit >= 1 and tol >= 0");
-    if (o->reorth != GKL_REORTH_FULL && o->reorth != GKL_REORTH_PARTIAL)
-        return set_err(h, GKL_ERR_ARG, "unknown reorthogonalisation mode %d", o->reorth);
-    if (!sigma) return set_err(h, GKL_ERR_ARG, "sigma must not be NULL");
-    if (o->v0 && !is_device_ptr(o->v0)) return set_err(h, GKL_ERR_ARG, "v0 must be device memory");
-    if ((Uout && !is_device_ptr(Uout)) || (Vout && !is_device_ptr(Vout)))
-        return set_err(h, GKL_ERR_ARG, "U and V must be device memory");
 
     struct EventPair {
         cudaEvent_t a = nullptr, b = nullptr;
@@ -399,8 +444,9 @@ static int run_svd(gkl_handle* h, const gkl_opts* o, double* sigma, T* Uout, T* 
                                           cudaMemcpyDeviceToDevice, h->stream),
                           "v restart copy")))
             return st;
-        if (o->reorth == GKL_REORTH_PARTIAL) {
-            // partial reorthogonalisation keeps v_ell only semi-orthogonal to V; restore it against the kept vectors
+        if (o->reorth == GKL_REORTH_PARTIAL || (o->reorth == GKL_REORTH_ONESIDED && n <= m)) {
+            // partial reorthogonalisation of the v side keeps v_ell only semi-orthogonal to V; restore it
+            // against the kept vectors
             if ((st = D.orthonormalise(D.V + (int64_t)kk * ldv, m, D.V, ldv, kk, ROLE_REPL_V, kk - 1, false,
                                        &sv.sc->scale_v)))
                 return st;
@@ -431,33 +477,24 @@ static int run_svd(gkl_handle* h, const gkl_opts* o, double* sigma, T* Uout, T* 
     if ((st = D.check(launch_rotate<T>(h->stream, D.U, ldu, ell, sv.P, ell, k, Uo, n, n), "U out"))) return st;
     if ((st = D.check(launch_rotate<T>(h->stream, D.V, ldv, ell, sv.Q, ell, k, Vo, m, m), "V out"))) return st;
     if ((st = D.check(launch_sign_fix<T>(h->stream, Uo, n, Vo, m, k, D.signs), "sign"))) return st;
-    if (Uout && (st = D.check(cudaMemcpyAsync(Uout, Uo, sizeof(T) * n * k, cudaMemcpyDeviceToDevice, h->stream),
-                              "U copy")))
+    // U, V out: device-to-device, or device-to-host with o->out_host
+    if (Uout && (st = D.check(cudaMemcpyAsync(Uout, Uo, sizeof(T) * n * k, cudaMemcpyDefault, h->stream), "U copy")))
         return st;
-    if (Vout && (st = D.check(cudaMemcpyAsync(Vout, Vo, sizeof(T) * m * k, cudaMemcpyDeviceToDevice, h->stream),
-                              "V copy")))
+    if (Vout && (st = D.check(cudaMemcpyAsync(Vout, Vo, sizeof(T) * m * k, cudaMemcpyDefault, h->stream), "V copy")))
         return st;
     cudaEventRecord(wall.b, h->stream);
     if ((st = D.check(cudaStreamSynchronize(h->stream), "final sync"))) return st;
-    if (h->tc_state > 0 && sizeof(T) == sizeof(float)) {
-        int terr = 0;
-        int* ew = reinterpret_cast<int*>(reinterpret_cast<char*>(h->aux) + kAuxErrOffset);
-        cudaMemcpyAsync(&terr, ew, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
-        if ((st = D.check(cudaStreamSynchronize(h->stream), "error word"))) return st;
-        if (terr) {
-            cudaMemsetAsync(ew, 0, sizeof(int), h->stream);
-            return set_err(h, GKL_ERR_CUDA, "tensor-core A^T u: a pipeline wait ran out (code %d)", terr);
-        }
-    }
+    if ((st = take_pending_error(h))) return st;
+    const int rank = numerical_rank(ho->sg, k, sv.eps_w);
     h->last_valid = converged ? 1 : 0;
     h->last_prec = sizeof(T) == 8 ? GKL_FP64 : GKL_FP32;
     h->last_k = k;
-    for (int i = 0; i < k; ++i) h->last_sigma[i] = ho->sg[i];
+    for (int i = 0; i < k; ++i) h->last_sigma[i] = i < rank ? ho->sg[i] : 0.0;
     h->last_next = k < ell ? ho->sg[k] : 0.0;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, wall.a, wall.b);
     for (int i = 0; i < k; ++i) {
-        sigma[i] = ho->sg[i];
+        sigma[i] = h->last_sigma[i];
         if (resid) resid[i] = ho->resid[i];
     }
     if (info) {
@@ -479,14 +516,19 @@ static int run_svd(gkl_handle* h, const gkl_opts* o, double* sigma, T* Uout, T* 
         info->jacobi_sweeps = max_sweeps;
         info->svd_fallbacks = hs.n_svd_fallback;
         info->svd_clusters = hs.n_svd_cluster;
-        info->reserved = 0;
+        info->rank = rank;
         info->ms_svd = D.ms_svd;
         info->ms_cgs = D.ms_cgs;
+        info->second_u = hs.second_u[1];
+        info->second_v = hs.second_v[1];
     }
     if (!converged) {
         set_err(h, GKL_NOT_CONVERGED, "not converged after %d cycles (max rel. residual %.3e)", cycle + 1, ho->maxrel);
         return GKL_NOT_CONVERGED;
     }
+    if (rank < k)
+        return set_err(h, GKL_RANK_DEFICIENT, "numerical rank %d < k = %d: sigma_%d.. reported as 0", rank, k,
+                       rank + 1);
     return GKL_OK;
 }
 
@@ -505,7 +547,9 @@ void gkl_opts_default(gkl_opts* o) {
     o->k = 10;
     o->ell = 30;
     o->k_keep = 0;
-    o->reorth = GKL_REORTH_FULL;
+    o->reorth = GKL_REORTH_DGKS;
+    o->out_host = 0;
+    o->reserved0 = 0;
     o->precision = GKL_FP64;
     o->maxit = 1000;
     o->profile = 0;
@@ -564,15 +608,13 @@ int gkl_init(gkl_handle** out, const uint8_t* packed, int64_t n, int64_t m, int6
         gkl_destroy(h);
         return GKL_ERR_CUDA;
     }
-    // FP32 A^T u runs on the N = 16 tcgen05 kernel; GKL_RMV_KERNEL=n256 selects
-    // the tcgen05 kernel with the codes on the N side and GKL_RMV_KERNEL=mma the
-    // mma.sync kernel (both kept for comparison)
-    const char* rk = std::getenv("GKL_RMV_KERNEL");
-    h->rmv_n256 = rk && std::strcmp(rk, "n256") == 0;
-    if (rk && std::strcmp(rk, "mma") == 0)
-        h->tc_state = -1;
-    else
-        tc_prepare(h);
+    // the FP32 A^T u runs on the tensor cores: TMA descriptor, kernel attributes
+    if (!tc_prepare(h)) {
+        cudaGetLastError();
+        set_err(nullptr, GKL_ERR_CUDA, "gkl_init: the tensor-core A^T u could not be prepared");
+        gkl_destroy(h);
+        return GKL_ERR_CUDA;
+    }
     if (mu) {
         e = cudaMemcpyAsync(h->mu, mu, sizeof(double) * m, cudaMemcpyDefault, h->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->d, scale, sizeof(double) * m, cudaMemcpyDefault, h->stream);
@@ -612,6 +654,7 @@ static int set_vec(gkl_handle* h, float** slot, const float* src, int64_t len, c
 
 int gkl_set_weights(gkl_handle* h, const float* s, const float* w) {
     if (!h) return set_err(nullptr, GKL_ERR_ARG, "NULL handle");
+    h->last_valid = 0;  // the stored triplets belong to the previous operator
     int st = set_vec(h, &h->s, s, h->n, "sample weights");
     if (st) return st;
     return set_vec(h, &h->w, w, h->m, "SNP weights");
@@ -646,12 +689,55 @@ int gkl_rmatvec(gkl_handle* h, int prec, const void* u, void* x) {
 int gkl_svd(gkl_handle* h, const gkl_opts* o, double* sigma, void* U, void* V, double* resid, gkl_info* info) {
     if (!h) return set_err(nullptr, GKL_ERR_ARG, "NULL handle");
     if (!o) return set_err(h, GKL_ERR_ARG, "NULL options");
+    if (o->reorth < GKL_REORTH_FULL || o->reorth > GKL_REORTH_ONESIDED)
+        return set_err(h, GKL_ERR_ARG, "unknown reorthogonalisation mode %d", o->reorth);
+    if (o->reserved0 != 0) return set_err(h, GKL_ERR_ARG, "gkl_opts.reserved0 must be 0");
+    if (!sigma) return set_err(h, GKL_ERR_ARG, "sigma must not be NULL");
+    if (o->v0 && mem_kind(o->v0, h->device) != MEM_DEVICE)
+        return set_err(h, GKL_ERR_ARG, "v0 must be device memory of the handle's GPU");
+    const int want = o->out_host ? MEM_HOST : MEM_DEVICE;
+    if ((U && mem_kind(U, h->device) != want) || (V && mem_kind(V, h->device) != want))
+        return set_err(h, GKL_ERR_ARG, o->out_host ? "out_host is set: U and V must be host memory"
+                                                   : "U and V must be device memory of the handle's GPU");
+    // a solve starts with no tensor-core wait recorded: one left over from earlier products
+    // (gkl_rmatvec without gkl_sync) is reported here instead of inside this solve
+    if (int pend = take_pending_error(h)) return pend;
+    h->last_valid = 0;
     if (o->precision == GKL_FP64)
         return run_svd<double>(h, o, sigma, (double*)U, (double*)V, resid, info);
     if (o->precision == GKL_FP32) return run_svd<float>(h, o, sigma, (float*)U, (float*)V, resid, info);
     if (o->precision == GKL_BLOCK || o->precision == GKL_BLOCK16)
         return run_block(h, o, sigma, (float*)U, (float*)V, resid, info);
     return set_err(h, GKL_ERR_ARG, "unknown precision %d", o->precision);
+}
+
+int gkl_scores(gkl_handle* h, void* S, int32_t out_host) {
+    if (!h) return set_err(nullptr, GKL_ERR_ARG, "NULL handle");
+    if (!h->last_valid || !h->last_U)
+        return set_err(h, GKL_ERR_STATE, "gkl_scores needs a successful gkl_svd with the current weights");
+    if (!S || mem_kind(S, h->device) != (out_host ? MEM_HOST : MEM_DEVICE))
+        return set_err(h, GKL_ERR_ARG, out_host ? "S must be host memory (out_host set)"
+                                                : "S must be device memory of the handle's GPU");
+    const int k = h->last_k;
+    const size_t esz = h->last_prec == GKL_FP64 ? sizeof(double) : sizeof(float);
+    const size_t bytes = esz * (size_t)h->n * k;
+    void* dst = S;
+    if (out_host) {
+        int st = ensure_scratch(h, bytes);
+        if (st) return st;
+        dst = h->scratch;
+    }
+    double* dsig = reinterpret_cast<double*>(reinterpret_cast<char*>(h->aux) + kAuxSigmaOffset);
+    cudaError_t e = cudaMemcpyAsync(dsig, h->last_sigma, sizeof(double) * k, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = launch_scores(h->stream, h->last_prec, h->last_U, dsig, h->n, k, dst);
+    if (e == cudaSuccess && out_host) e = cudaMemcpyAsync(S, dst, bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // dsig is read from pageable host memory
+    return e == cudaSuccess ? GKL_OK : cuda_err(h, e, "scores");
+}
+
+int gkl_sync(gkl_handle* h) {
+    if (!h) return set_err(nullptr, GKL_ERR_ARG, "NULL handle");
+    return take_pending_error(h);
 }
 
 int gkl_destroy(gkl_handle* h) {

@@ -216,172 +216,6 @@ __global__ void __launch_bounds__(128) k_ptm(const double* __restrict__ P, const
 
 // ---- batched block products (every code decoded once for all q vectors) -------
 
-// X[:, 0:q] = A^T U[:, 0:q] (q <= 32), FP32.  A block owns 128 SNPs and all q
-// vectors: thread (pair p, group g) accumulates SNPs 2p, 2p+1 x vectors
-// 8g..8g+7 over all samples, x_{j,c} = d_j w_j sum_i t_j(c_ij) s_i U[i, c] with
-// t_j(c) = c - mu_j (observed), 0 (missing).  Per step the block stages the
-// packed codes of 64 samples (16 bytes of each of its 128 rows) and the 64
-// matching rows of s o U in shared memory.
-__global__ void __launch_bounds__(256) k_block_rmv(const uint8_t* __restrict__ packed, int64_t stride, int64_t n,
-                                                    int64_t m, const double* __restrict__ mu,
-                                                    const double* __restrict__ d, const float* __restrict__ w,
-                                                    const float* __restrict__ s, const float* __restrict__ U,
-                                                    int64_t ldu, int q, float* __restrict__ X, int64_t ldx) {
-    __shared__ __align__(16) uint32_t sc[128][5];   // 16 bytes of codes per row (+ pad)
-    __shared__ __align__(16) float su[64][32];      // s_i U[i, c] (rows 128 B: aligned float4 reads)
-    const int tid = threadIdx.x, pair = tid & 63, g = tid >> 6;
-    const int64_t j0 = (int64_t)blockIdx.x * 128;
-    const int64_t ja = j0 + 2 * pair, jb = ja + 1;
-    const float mua = ja < m ? (float)mu[ja] : 0.f, mub = jb < m ? (float)mu[jb] : 0.f;
-    // per 64-sample step an FP32 partial, added into hi with Kahan compensation lo
-    float acc[2][8], hi[2][8], lo[2][8];
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) hi[r][c] = lo[r][c] = 0.f;
-    for (int64_t i0 = 0; i0 < n; i0 += 64) {
-        __syncthreads();
-        // codes: thread t loads 16 bytes of row t/2 (two threads per row, 8 bytes each)
-        {
-            const int row = tid >> 1, half = tid & 1;
-            const int64_t jr = j0 + row, boff = i0 / 4 + 8 * half;
-            uint2 v = make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
-            if (jr < m && boff + 8 <= stride)
-                v = *reinterpret_cast<const uint2*>(packed + jr * stride + boff);
-            sc[row][2 * half] = v.x;
-            sc[row][2 * half + 1] = v.y;
-        }
-        for (int e = tid; e < 64 * 32; e += 256) {
-            const int r = e & 63, c = e >> 6;  // consecutive threads: consecutive samples of one column
-            const int64_t i = i0 + r;
-            float v = 0.f;
-            if (i < n && c < q) v = U[i + (int64_t)c * ldu] * (s ? s[i] : 1.f);
-            su[r][c] = v;
-        }
-        __syncthreads();
-        if (8 * g >= q) continue;
-#pragma unroll
-        for (int r = 0; r < 2; ++r)
-#pragma unroll
-            for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
-#pragma unroll 4
-        for (int wd = 0; wd < 4; ++wd) {
-            const uint32_t wa = sc[2 * pair][wd], wb = sc[2 * pair + 1][wd];
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const uint32_t ca = (wa >> (2 * k)) & 3u, cb = (wb >> (2 * k)) & 3u;
-                const float ta = ca == 3u ? 0.f : (float)ca - mua, tb = cb == 3u ? 0.f : (float)cb - mub;
-                const float4 u0 = *reinterpret_cast<const float4*>(&su[16 * wd + k][8 * g]);
-                const float4 u1 = *reinterpret_cast<const float4*>(&su[16 * wd + k][8 * g + 4]);
-                const float uu[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    acc[0][c] = fmaf(ta, uu[c], acc[0][c]);
-                    acc[1][c] = fmaf(tb, uu[c], acc[1][c]);
-                }
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < 2; ++r)
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const float y = acc[r][c] - lo[r][c], t = hi[r][c] + y;
-                lo[r][c] = (t - hi[r][c]) - y;
-                hi[r][c] = t;
-            }
-    }
-    const int64_t jj[2] = {ja, jb};
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        if (jj[r] >= m) continue;
-        double dw = d[jj[r]];
-        if (w) dw *= (double)w[jj[r]];
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-            if (8 * g + c < q) X[jj[r] + (int64_t)(8 * g + c) * ldx] = (float)(dw * ((double)hi[r][c] - (double)lo[r][c]));
-    }
-}
-
-// Partials of Y = A V (V m x q, q <= 32) over SNP chunk blockIdx.y: thread
-// (group p, vector group g) owns samples 8p..8p+7 of the block's 512 and
-// vectors 8g..8g+7; part[chunk][c][i] = sum_{j in chunk} t_j(c_ij) V[j, c] with
-// t_j(c) = (c - mu_j) d_j w_j (observed), 0 (missing).  V rows and the per-SNP
-// coefficients are staged 64 SNPs at a time.
-__global__ void __launch_bounds__(256) k_block_mv_part(const uint8_t* __restrict__ packed, int64_t stride, int64_t n,
-                                                        int64_t m, int64_t rpc, const double* __restrict__ mu,
-                                                        const double* __restrict__ d, const float* __restrict__ w,
-                                                        const float* __restrict__ V, int64_t ldv, int q,
-                                                        float* __restrict__ part, int64_t ldp) {
-    __shared__ __align__(16) float sv[64][32];  // rows 128 B: aligned float4 reads
-    __shared__ float sa[64], sb[64];  // t = code * sa - sb for observed codes
-    const int tid = threadIdx.x, p = tid & 63, g = tid >> 6;
-    const int64_t i0 = (int64_t)blockIdx.x * 512 + 8 * p;  // first of this thread's 8 samples
-    const int64_t j0 = (int64_t)blockIdx.y * rpc, j1 = min(m, j0 + rpc);
-    float acc[8][8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) acc[k][c] = 0.f;
-    for (int64_t jb = j0; jb < j1; jb += 64) {
-        const int nr = (int)min((int64_t)64, j1 - jb);
-        __syncthreads();
-        for (int e = tid; e < 64 * 32; e += 256) {
-            const int r = e & 63, c = e >> 6;  // consecutive threads: consecutive SNPs of one column
-            sv[r][c] = (r < nr && c < q) ? V[(jb + r) + (int64_t)c * ldv] : 0.f;
-        }
-        if (tid < 64) {
-            float a = 0.f, b = 0.f;
-            if (tid < nr) {
-                double dw = d[jb + tid];
-                if (w) dw *= (double)w[jb + tid];
-                a = (float)dw;
-                b = (float)(mu[jb + tid] * dw);
-            }
-            sa[tid] = a;
-            sb[tid] = b;
-        }
-        __syncthreads();
-        if (8 * g >= q) continue;
-        for (int r = 0; r < nr; ++r) {
-            const int64_t boff = (jb + r) * stride + i0 / 4;
-            const uint32_t cw = (i0 < n && i0 / 4 + 2 <= stride) ? (uint32_t)__ldg(reinterpret_cast<const unsigned short*>(packed + boff))
-                                                                 : 0xFFFFu;
-            const float a = sa[r], b = sb[r];
-            const float4 v0 = *reinterpret_cast<const float4*>(&sv[r][8 * g]);
-            const float4 v1 = *reinterpret_cast<const float4*>(&sv[r][8 * g + 4]);
-            const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const uint32_t cd = (cw >> (2 * k)) & 3u;
-                const float t = cd == 3u ? 0.f : fmaf((float)cd, a, -b);
-#pragma unroll
-                for (int c = 0; c < 8; ++c) acc[k][c] = fmaf(t, vv[c], acc[k][c]);
-            }
-        }
-    }
-    if (8 * g >= q) return;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        if (8 * g + c >= q) break;
-        float* out = part + (int64_t)blockIdx.y * ldp * q + (int64_t)(8 * g + c) * ldp;
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            if (i0 + k < n) out[i0 + k] = acc[k][c];
-    }
-}
-
-// Y[i, c] = s_i sum_chunk part[chunk][c][i] (fixed order).
-__global__ void k_block_mv_fin(const float* __restrict__ part, int64_t ldp, int chunks, int64_t n, int q,
-                               const float* __restrict__ s, float* __restrict__ Y, int64_t ldy) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n * q) return;
-    const int64_t i = e % n, c = e / n;
-    float t = 0.f;
-    for (int ch = 0; ch < chunks; ++ch) t += part[(int64_t)ch * ldp * q + c * ldp + i];
-    if (s) t *= s[i];
-    Y[i + c * ldy] = t;
-}
-
 // ---- host linear algebra (b x b, FP64) -----------------------------------------
 
 // Symmetric eigen-decomposition by cyclic Jacobi: G = Z diag(lam) Z^T.
@@ -471,8 +305,7 @@ struct BlockCtx {
     cudaStream_t st;
     double* d_part;    // Gram partials
     double* d_small;   // p x q FP64 results / coefficient uploads
-    float* d_bpart;    // A V partials of the batched product
-    void* tc_scratch;  // tensor-core products: digit tiles, partials (null: SIMT kernels)
+    void* tc_scratch;  // tensor-core products: digit tiles, partials
     int tc_digits;     // digits per vector of the tensor-core products
     int nblk_max;
     uint64_t seed;
@@ -484,7 +317,7 @@ struct BlockCtx {
     // profile: CUDA events around each main tensor-core kernel (pairs), kept
     // until the solve's final synchronisation
     bool profile = false;
-    bool cgs2_always = false;  // GKL_BLOCK_CGS=2: always two Gram-Schmidt passes
+    bool cgs2_always = false;  // GKL_REORTH_FULL: always two Gram-Schmidt passes
     std::vector<cudaEvent_t> ev_mv, ev_rmv;
     cudaEvent_t next_event(std::vector<cudaEvent_t>& pool, size_t& used) {
         if (used == pool.size()) {
@@ -674,60 +507,28 @@ static cudaError_t orthonormalize_once(BlockCtx& c, float* X, int64_t ldx, int q
     return cudaGetLastError();
 }
 
-// Y[:, 0:q] = A X[:, 0:q] (forward) or A^T X (transpose) with the batched kernels.
-constexpr size_t kBlockPartBytes = 64u << 20;  // A V partials (chunks x q x n floats)
-
-static void mv_chunks(const gkl_handle* h, int q, int& tiles, int& chunks, int64_t& rpc, int64_t& ldp) {
-    tiles = (int)((h->n + 511) / 512);
-    ldp = (h->n + 31) / 32 * 32;
-    const int64_t cap = std::max<int64_t>(1, (int64_t)(kBlockPartBytes / (sizeof(float) * (size_t)q * (size_t)ldp)));
-    const int64_t want = std::max<int64_t>(1, (4 * (int64_t)h->num_sms + tiles - 1) / tiles);
-    int64_t ch = std::min<int64_t>({want, cap, (h->m + 63) / 64});
-    rpc = (h->m + ch - 1) / ch;
-    rpc = (rpc + 63) / 64 * 64;
-    chunks = (int)((h->m + rpc - 1) / rpc);
-}
-
+// Y[:, 0:q] = A X[:, 0:q] (forward) or A^T X (transpose) on the tensor cores, at
+// most 128 / D vectors per pass.
 static cudaError_t block_product(BlockCtx& c, bool transpose, const float* X, int64_t ldx, float* Y, int64_t ldy,
                                  int q) {
     gkl_handle* h = c.h;
-    if (c.tc_scratch) {
-        // tensor cores: at most 128 / D vectors per pass
-        const int per = 128 / c.tc_digits;
-        for (int c0 = 0; c0 < q; c0 += per) {
-            int nl = 0;
-            cudaEvent_t e0 = nullptr, e1 = nullptr;
-            if (c.profile) {
-                auto& pool = transpose ? c.ev_rmv : c.ev_mv;
-                auto& used = transpose ? c.used_rmv : c.used_mv;
-                e0 = c.next_event(pool, used);
-                e1 = c.next_event(pool, used);
-            }
-            cudaError_t e = launch_block_product_tc(h, transpose, X + (int64_t)c0 * ldx, ldx, std::min(per, q - c0),
-                                                    c.tc_digits, Y + (int64_t)c0 * ldy, ldy, c.tc_scratch, &nl, e0,
-                                                    e1);
-            if (e != cudaSuccess) return e;
-            c.launches += nl;
+    const int per = 128 / c.tc_digits;
+    for (int c0 = 0; c0 < q; c0 += per) {
+        int nl = 0;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (c.profile) {
+            auto& pool = transpose ? c.ev_rmv : c.ev_mv;
+            auto& used = transpose ? c.used_rmv : c.used_mv;
+            e0 = c.next_event(pool, used);
+            e1 = c.next_event(pool, used);
         }
-        if (!transpose) c.products += q;
-        return cudaSuccess;
+        cudaError_t e = launch_block_product_tc(h, transpose, X + (int64_t)c0 * ldx, ldx, std::min(per, q - c0),
+                                                c.tc_digits, Y + (int64_t)c0 * ldy, ldy, c.tc_scratch, &nl, e0, e1);
+        if (e != cudaSuccess) return e;
+        c.launches += nl;
     }
-    if (transpose) {
-        k_block_rmv<<<(unsigned)((h->m + 127) / 128), 256, 0, c.st>>>(h->packed, h->stride, h->n, h->m, h->mu, h->d,
-                                                                        h->w, h->s, X, ldx, q, Y, ldy);
-        c.launches += 1;
-    } else {
-        int tiles, chunks;
-        int64_t rpc, ldp;
-        mv_chunks(h, q, tiles, chunks, rpc, ldp);
-        k_block_mv_part<<<dim3((unsigned)tiles, (unsigned)chunks), 256, 0, c.st>>>(
-            h->packed, h->stride, h->n, h->m, rpc, h->mu, h->d, h->w, X, ldx, q, c.d_bpart, ldp);
-        k_block_mv_fin<<<(unsigned)((h->n * q + 255) / 256), 256, 0, c.st>>>(c.d_bpart, ldp, chunks, h->n, q, h->s, Y,
-                                                                              ldy);
-        c.launches += 2;
-        c.products += q;
-    }
-    return cudaGetLastError();
+    if (!transpose) c.products += q;
+    return cudaSuccess;
 }
 
 static int64_t round32(int64_t x) { return (x + 31) / 32 * 32; }
@@ -766,16 +567,11 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
                  oSmall = take(sizeof(double) * 2 * GKL_MAX_ELL * kMaxB), oSigns = take(sizeof(int) * GKL_MAX_ELL);
     const size_t oOutU = take(sizeof(float) * n * k), oOutV = take(sizeof(float) * m * k);
     // products: tcgen05 with 8 digits per vector (finer than FP32), or 4 digits
-    // (GKL_BLOCK16) during the iteration, where the handle supports them
-    // (GKL_BLOCK_PRODUCTS=simt selects the SIMT kernels)
-    const char* bpk = getenv("GKL_BLOCK_PRODUCTS");
-    const bool use_tc = !(bpk && strcmp(bpk, "simt") == 0) && block_tc_prepare(h);
+    // (GKL_BLOCK16) during the iteration
+    if (!block_tc_prepare(h))
+        return set_err(h, GKL_ERR_ARG, "the block form needs the tensor-core products (n <= 524,000 samples)");
     const int tc_digits = o->precision == GKL_BLOCK16 ? 4 : 8;
-    int mvt, mvc;
-    int64_t mvr, mvl;
-    mv_chunks(h, b, mvt, mvc, mvr, mvl);
-    const size_t oBpart = use_tc ? take(block_tc_scratch_bytes(h, kMaxB))
-                                 : take(sizeof(float) * (size_t)mvc * (size_t)b * (size_t)mvl);
+    const size_t oBpart = take(block_tc_scratch_bytes(h, kMaxB));
     void* ws = nullptr;
     if (cudaMalloc(&ws, off) != cudaSuccess) return set_err(h, GKL_ERR_CUDA, "block workspace of %zu bytes", off);
     char* W = static_cast<char*>(ws);
@@ -805,8 +601,7 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
                h->stream,
                reinterpret_cast<double*>(W + oPart),
                reinterpret_cast<double*>(W + oSmall),
-               use_tc ? nullptr : reinterpret_cast<float*>(W + oBpart),
-               use_tc ? static_cast<void*>(W + oBpart) : nullptr,
+               static_cast<void*>(W + oBpart),
                tc_digits,
                nblk,
                o->seed,
@@ -815,11 +610,8 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
                0,
                0,
                0};
-    c.profile = o->profile != 0 && use_tc;
-    {
-        const char* bc = getenv("GKL_BLOCK_CGS");
-        c.cgs2_always = bc && strcmp(bc, "2") == 0;
-    }
+    c.profile = o->profile != 0;
+    c.cgs2_always = o->reorth == GKL_REORTH_FULL;
     cudaError_t e = cudaMemsetAsync(sv.sc, 0, sizeof(DevScal), c.st);
     cudaEvent_t ev0, ev1;
     cudaEventCreate(&ev0);
@@ -830,10 +622,6 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
     CycleOut* ho = h->host_out;
     int cycle = 0, restarts = 0, converged = 0, svd_fb = 0, svd_fp64 = 0, max_sweeps = 0, svd_unrefined = 0,
         svd_uncontracted = 0;
-    // GKL_BLOCK_SVD=fp64: where the FP64 refinement of the projected SVD does not
-    // apply, take the FP64 Jacobi at every cycle (not only the last)
-    const char* bsv = getenv("GKL_BLOCK_SVD");
-    const bool svd_fp64_always = bsv && strcmp(bsv, "fp64") == 0;
     double maxrel = 0.0, dtheta = 0.0;
     std::vector<double> res(k, 0.0);
     auto fail = [&](const char* what) {
@@ -929,10 +717,10 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
             return cudaSuccess;
         };
         if ((e = upload(c, T, sv.B)) != cudaSuccess) return fail("T upload");
-        if ((e = projected(svd_fp64_always)) != cudaSuccess) return fail("projected SVD");
+        if ((e = projected(false)) != cudaSuccess) return fail("projected SVD");
         if (svd_fb) ++svd_unrefined;
         if (ho->svd_unconverged) ++svd_uncontracted;
-        if ((converged || cycle == o->maxit - 1) && svd_fb && !svd_fp64_always) {
+        if ((converged || cycle == o->maxit - 1) && svd_fb) {
             ++svd_fp64;
             if ((e = projected(true)) != cudaSuccess) return fail("projected SVD (FP64)");
         }
@@ -1029,37 +817,52 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
         if (e == cudaSuccess) e = launch_rotate<float>(c.st, V, ldv, ell, sv.Q, ell, k, Vo, m, m);
     }
     if (e == cudaSuccess) e = launch_sign_fix<float>(c.st, Uo, n, Vo, m, k, reinterpret_cast<int*>(W + oSigns));
-    if (e == cudaSuccess && Uout) e = cudaMemcpyAsync(Uout, Uo, sizeof(float) * n * k, cudaMemcpyDeviceToDevice, c.st);
-    if (e == cudaSuccess && Vout) e = cudaMemcpyAsync(Vout, Vo, sizeof(float) * m * k, cudaMemcpyDeviceToDevice, c.st);
+    // U, V out (device-to-device, or to host memory with o->out_host); the
+    // triplets also stay in the handle for gkl_scores and gkl_grad
+    if (e == cudaSuccess && Uout) e = cudaMemcpyAsync(Uout, Uo, sizeof(float) * n * k, cudaMemcpyDefault, c.st);
+    if (e == cudaSuccess && Vout) e = cudaMemcpyAsync(Vout, Vo, sizeof(float) * m * k, cudaMemcpyDefault, c.st);
+    const size_t lb = sizeof(float) * (size_t)(n + m) * k;
+    if (e == cudaSuccess && h->last_bytes < lb) {
+        if (h->last_U) cudaFree(h->last_U);
+        h->last_U = nullptr;
+        h->last_bytes = 0;
+        e = cudaMalloc(&h->last_U, lb);
+        if (e == cudaSuccess) h->last_bytes = lb;
+    }
+    if (e == cudaSuccess) {
+        h->last_V = static_cast<char*>(h->last_U) + sizeof(float) * (size_t)n * k;
+        e = cudaMemcpyAsync(h->last_U, Uo, sizeof(float) * n * k, cudaMemcpyDeviceToDevice, c.st);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->last_V, Vo, sizeof(float) * m * k, cudaMemcpyDeviceToDevice, c.st);
     cudaEventRecord(ev1, c.st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
     if (e != cudaSuccess) return fail("output");
-    if (use_tc) {
-        int terr = 0;
-        int* ew = reinterpret_cast<int*>(reinterpret_cast<char*>(h->aux) + kAuxErrOffset);
-        e = cudaMemcpy(&terr, ew, sizeof(int), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return fail("error word");
-        if (terr) {
-            cudaMemset(ew, 0, sizeof(int));
-            cudaFree(ws);
-            cudaEventDestroy(ev0);
-            cudaEventDestroy(ev1);
-            return set_err(h, GKL_ERR_CUDA, "tensor-core block product: a pipeline wait ran out (code %d)", terr);
-        }
+    if (int pend = take_pending_error(h)) {
+        cudaFree(ws);
+        cudaEventDestroy(ev0);
+        cudaEventDestroy(ev1);
+        return pend;
     }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev0, ev1);
+    const int rank = numerical_rank(sg.data(), k, sv.eps_w);
     for (int i = 0; i < k; ++i) {
-        sigma[i] = sg[i];
+        sigma[i] = i < rank ? sg[i] : 0.0;
         if (resid) resid[i] = res[i];
     }
+    h->last_valid = converged ? 1 : 0;
+    h->last_prec = GKL_FP32;
+    h->last_k = k;
+    for (int i = 0; i < k; ++i) h->last_sigma[i] = sigma[i];
+    h->last_next = k < ell ? sg[k] : 0.0;
     if (info) {
         std::memset(info, 0, sizeof(*info));
         info->matvec_pairs = c.products;
         info->restarts = restarts;
         info->cycles = cycle + 1;
         info->breakdowns = c.deflations;
-        info->reorth_v = c.cgs_second;  // block form: orthonormalisations that needed a second CGS pass
+        info->second_v = c.cgs_second;  // block form: orthonormalisations that needed a second CGS pass
+        info->rank = rank;
         info->converged = converged;
         info->max_rel_resid = maxrel;
         info->dtheta1 = dtheta;
@@ -1067,18 +870,20 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
         info->launches = c.launches + 5;
         info->svd_fallbacks = svd_fp64;
         info->svd_clusters = svd_unrefined;  // cycles whose projected SVD could not be refined
-        info->reorth_u = svd_uncontracted;   // ... of which because the refinement did not contract
         if (c.profile) {  // main tensor-core product kernels, summed
             info->ms_mv = sum_event_pairs(c.ev_mv, c.used_mv, &info->n_mv);
             info->ms_rmv = sum_event_pairs(c.ev_rmv, c.used_rmv, &info->n_rmv);
         }
         info->jacobi_sweeps = max_sweeps;
     }
-    h->last_valid = 0;  // gkl_grad works from the single-vector solvers' triplets
     cudaFree(ws);
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
-    return converged ? GKL_OK : GKL_NOT_CONVERGED;
+    if (!converged) return set_err(h, GKL_NOT_CONVERGED, "block form not converged after %d cycles", cycle + 1);
+    if (rank < k)
+        return set_err(h, GKL_RANK_DEFICIENT, "numerical rank %d < k = %d: sigma_%d.. reported as 0", rank, k,
+                       rank + 1);
+    return GKL_OK;
 }
 
 }  // namespace gkl

@@ -179,6 +179,15 @@ __device__ inline void reset_estimates(double* est, int L, int row, int upto, do
     }
 }
 
+// Whether the u (side 0) or v (side 1) vectors are reorthogonalised at every
+// step: FULL and DGKS both sides; ONESIDED the shorter side (u if n <= m);
+// PARTIAL neither (the omega-recurrence decides).
+__device__ __forceinline__ bool always_reorth(const Sv& sv, int side) {
+    if (sv.reorth == GKL_REORTH_FULL || sv.reorth == GKL_REORTH_DGKS) return true;
+    if (sv.reorth == GKL_REORTH_ONESIDED) return side == 0 ? sv.n <= sv.m : sv.n > sv.m;
+    return false;
+}
+
 // Scalar logic after ||x||^2 of the current vector is known.  Called by all
 // threads of the last block.
 __device__ inline void step_epilogue(const Sv& sv, int role, int j, double nrm2) {
@@ -191,7 +200,7 @@ __device__ inline void step_epilogue(const Sv& sv, int role, int j, double nrm2)
         const int ncols = j;
         int forced = 0, trig = 0;
         if (ncols > 0) {
-            if (sv.reorth == GKL_REORTH_FULL) {
+            if (always_reorth(sv, 0)) {
                 forced = 1;
             } else {
                 forced = sc->force_u || j == sv.kk_start;
@@ -203,7 +212,7 @@ __device__ inline void step_epilogue(const Sv& sv, int role, int j, double nrm2)
             s_do = forced || trig;
             sc->pre = nrm;
             sc->reorth_u = s_do;
-            sc->force_u = (sv.reorth == GKL_REORTH_PARTIAL) && trig;
+            sc->force_u = !always_reorth(sv, 0) && trig;
             if (s_do) sc->n_reorth_u += 1;
             else finalize_alpha(sv, j, nrm, nrm);
         }
@@ -215,7 +224,7 @@ __device__ inline void step_epilogue(const Sv& sv, int role, int j, double nrm2)
         break;
     case ROLE_V_PRE: {
         int forced = 0, trig = 0;
-        if (sv.reorth == GKL_REORTH_FULL) {
+        if (always_reorth(sv, 1)) {
             forced = 1;
         } else {
             forced = sc->force_v || j == sv.kk_start;
@@ -226,7 +235,7 @@ __device__ inline void step_epilogue(const Sv& sv, int role, int j, double nrm2)
             s_do = forced || trig;
             sc->pre = nrm;
             sc->reorth_v = s_do;
-            sc->force_v = (sv.reorth == GKL_REORTH_PARTIAL) && trig;
+            sc->force_v = !always_reorth(sv, 1) && trig;
             if (s_do) sc->n_reorth_v += 1;
             else finalize_beta(sv, j, nrm, nrm);
         }

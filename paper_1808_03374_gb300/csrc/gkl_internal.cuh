@@ -29,6 +29,8 @@ struct DevScal {
     int svd_fallback;         // projected SVD: 1 = FP32 + refinement does not apply, use FP64 Jacobi
     int n_svd_fallback;       // cycles whose projected SVD used the FP64 Jacobi
     int n_svd_cluster;        // ... of which because of clustered or tiny values
+    int second_u[2];          // adaptive second Gram-Schmidt pass of the u side: {take it now, times taken}
+    int second_v[2];          // ... of the v side
 };
 
 enum { ABORT_NONE = 0, ABORT_BREAKDOWN = 1, ABORT_NONFINITE = 2 };
@@ -99,9 +101,8 @@ struct gkl_handle {
     size_t last_bytes;
     void* gws;         // gradient workspace (grown on demand)
     size_t gws_bytes;
-    // tensor-core (tcgen05) A^T u: 0 = not prepared, 1 = ready, -1 = unavailable or disabled
+    // tensor-core (tcgen05) A^T u: 0 = not prepared, 1 = ready, -1 = unavailable
     int tc_state;
-    int rmv_n256;  // 1: the N = 256 tensor-core kernel (k_rmv_n256) instead of the N = 16 one (k_rmv_tc)
     alignas(64) unsigned char tc_map[128];  // TMA descriptor of the packed matrix
     int64_t* miss_off;   // CSR of the missing codes per SNP (m + 1 offsets), built by tc_prepare
     uint32_t* miss_idx;  // sample indices, ascending per SNP
@@ -148,18 +149,20 @@ cudaError_t launch_matvec(const gkl_handle* h, const T* v, T* y, void* scratch, 
 template <typename T>
 cudaError_t launch_rmatvec(const gkl_handle* h, const T* u, T* x, void* scratch, const Sv* sv, const FinArgs* fa,
                            cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, int* nlaunch = nullptr);
-// Tensor-core A^T u (FP32 path, packed_mma.cu).
-size_t rmv_mma_scratch_bytes(const gkl_handle* h);
-cudaError_t launch_rmatvec_mma(const gkl_handle* h, const float* u, float* x, void* scratch, const Sv* sv,
-                               const FinArgs* fa, cudaEvent_t ev0, cudaEvent_t ev1, int* nlaunch);
 constexpr size_t kAuxBytes = 64 * 1024;
-constexpr size_t kAuxErrOffset = 60 * 1024;  // int: nonzero if a tensor-core kernel's wait ran out
-// Shared by the two tensor-core A^T u paths (defined in packed_mma.cu).
-__global__ void __launch_bounds__(256) k_u_scale(const float* u, const float* s, int64_t n, double* part,
-                                                  unsigned* counter, double* dsc);
-__global__ void __launch_bounds__(256) k_rmv_mma_fin(const double* p1, const double* p3, int nb, int64_t m,
-                                                      const double* mu, const double* d, const float* w,
-                                                      const double* dsc, float* x, FinArgs fa, Sv sv);
+constexpr size_t kAuxErrOffset = 60 * 1024;    // int: nonzero if a tensor-core kernel's wait ran out
+constexpr size_t kAuxSigmaOffset = 48 * 1024;  // GKL_MAX_ELL doubles: singular values for gkl_scores
+// Synchronise the handle's stream; GKL_ERR_CUDA (message set, record cleared) if
+// a tensor-core kernel's bounded wait ran out since the last check.
+int take_pending_error(gkl_handle* h);
+int numerical_rank(const double* sg, int k, double eps_w);
+// Kind of a pointer as the library accepts it: device (or managed) memory of
+// `device`, host memory (pageable, pinned or registered), or neither (device
+// memory of another GPU, or an invalid pointer).
+enum MemKind { MEM_BAD = 0, MEM_DEVICE = 1, MEM_HOST = 2 };
+int mem_kind(const void* p, int device);
+// S = U diag(sigma) (n x k, column-major) in the type of prec (GKL_FP64: double, else float)
+cudaError_t launch_scores(cudaStream_t st, int prec, const void* U, const double* sigma, int64_t n, int k, void* S);
 // tcgen05 A^T u (FP32 path, packed_tc.cu); tc_prepare builds the missing-code list once per handle.
 bool tc_prepare(gkl_handle* h);
 size_t rmv_tc_scratch_bytes(const gkl_handle* h);
@@ -184,9 +187,10 @@ enum {
 enum { CGS_DOTS = 0, CGS_UPD_DOTS = 1, CGS_UPD_NORM = 2, CGS_FILL_DOTS = 3 };
 int cgs_grid(int64_t len, int num_sms);
 
+// second: null = both Gram-Schmidt passes; else the adaptive second pass (flag and count, see k_cgs)
 template <typename T>
 cudaError_t launch_cgs(const Sv& sv, cudaStream_t st, int mode, T* x, int64_t len, const T* W, int64_t ldw, int ncols,
-                       const int* cond, int role, int j, uint32_t draw, int num_sms);
+                       const int* cond, int role, int j, uint32_t draw, int num_sms, int* second = nullptr);
 template <typename T>
 cudaError_t launch_scale(const Sv& sv, cudaStream_t st, T* x, int64_t len, const double* scale);
 template <typename T>

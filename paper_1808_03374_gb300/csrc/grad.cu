@@ -276,7 +276,8 @@ static int run_grad(gkl_handle* h, const double* sigma_bar, const T* Sbar, T* g_
             if ((st = G.check(cudaGetLastError(), "g_s"))) return st;
         }
     }
-    return G.check(cudaStreamSynchronize(h->stream), "gradient");
+    if ((st = G.check(cudaStreamSynchronize(h->stream), "gradient"))) return st;
+    return take_pending_error(h);  // a tensor-core product whose bounded wait ran out
 }
 
 }  // namespace gkl
@@ -286,7 +287,9 @@ using namespace gkl;
 extern "C" int gkl_grad(gkl_handle* h, const double* sigma_bar, const void* scores_bar, void* g_w, void* g_s,
                         double min_relgap) {
     if (!h) return set_err(nullptr, GKL_ERR_ARG, "NULL handle");
-    if (!h->last_valid) return set_err(h, GKL_ERR_STATE, "gkl_grad needs a converged gkl_svd on this handle first");
+    if (!h->last_valid)
+        return set_err(h, GKL_ERR_STATE,
+                       "gkl_grad needs a converged gkl_svd on this handle, with the current weights, first");
     if (!g_w && !g_s) return set_err(h, GKL_ERR_ARG, "nothing to compute: g_w and g_s are both NULL");
     if (!(min_relgap >= 0.0)) return set_err(h, GKL_ERR_ARG, "min_relgap must be >= 0");
     if (h->last_prec == GKL_FP64)

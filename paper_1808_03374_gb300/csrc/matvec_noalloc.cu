@@ -45,14 +45,9 @@ int scratch_address(int dev, void** out) {
     return GKL_OK;
 }
 
-bool on_device(const void* p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+// Device (or managed) memory of device `dev`: memory of another GPU would turn
+// into peer reads or a fault inside the kernels.
+bool on_device(const void* p, int dev) { return gkl::mem_kind(p, dev) == gkl::MEM_DEVICE; }
 
 }  // namespace
 
@@ -66,8 +61,6 @@ extern "C" int gkl_matvec_noalloc(const uint8_t* packed, int64_t n, int64_t m, i
         return set_err(nullptr, GKL_ERR_ARG, "stride must be a multiple of 16 and >= ceil(n/4)");
     if (((uintptr_t)packed & 15u) != 0) return set_err(nullptr, GKL_ERR_ARG, "packed must be 16-byte aligned");
     if (prec != GKL_FP64 && prec != GKL_FP32) return set_err(nullptr, GKL_ERR_ARG, "unknown precision %d", prec);
-    if (!on_device(packed) || !on_device(mu) || !on_device(scale) || !on_device(v) || !on_device(y))
-        return set_err(nullptr, GKL_ERR_ARG, "packed, mu, scale, v and y must be device memory");
 
     gkl_handle h{};
     h.packed = packed;
@@ -78,6 +71,10 @@ extern "C" int gkl_matvec_noalloc(const uint8_t* packed, int64_t n, int64_t m, i
     cudaError_t e = cudaGetDevice(&h.device);
     if (e != cudaSuccess) return gkl::cuda_err(nullptr, e, "cudaGetDevice");
     if (h.device < 0 || h.device >= kMaxDevices) return set_err(nullptr, GKL_ERR_ARG, "device index out of range");
+    const int dev = h.device;
+    if (!on_device(packed, dev) || !on_device(mu, dev) || !on_device(scale, dev) || !on_device(v, dev) ||
+        !on_device(y, dev))
+        return set_err(nullptr, GKL_ERR_ARG, "packed, mu, scale, v and y must be device memory of the current GPU");
     e = cudaDeviceGetAttribute(&h.num_sms, cudaDevAttrMultiProcessorCount, h.device);
     if (e != cudaSuccess) return gkl::cuda_err(nullptr, e, "cudaDeviceGetAttribute");
     h.mu = const_cast<double*>(mu);

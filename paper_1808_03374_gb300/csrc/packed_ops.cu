@@ -112,8 +112,7 @@ MvPlan plan_products(const gkl_handle* h) {
     }
     size_t mv = (size_t)std::max(p.chunks, p.pair_chunks) * (size_t)p.ldp + (size_t)h->m * 4;  // partials + LUT
     size_t rmv = 2 * (size_t)p.tiles * (size_t)h->m;
-    size_t tc = h->aux ? rmv_mma_scratch_bytes(h) : 0;
-    if (h->tc_state > 0) tc = std::max(tc, rmv_tc_scratch_bytes(h));
+    size_t tc = h->tc_state > 0 ? rmv_tc_scratch_bytes(h) : 0;
     p.bytes_fp64 = std::max(std::max(mv, rmv) * sizeof(double) + 256, tc);
     return p;
 }
@@ -524,30 +523,29 @@ template <typename T>
 cudaError_t launch_rmatvec(const gkl_handle* h, const T* u, T* x, void* scratch, const Sv* sv, const FinArgs* fa,
                            cudaEvent_t ev0, cudaEvent_t ev1, int* nlaunch) {
     if constexpr (sizeof(T) == sizeof(float)) {
-        if (h->aux && h->tc_state > 0)
-            return launch_rmatvec_tc(h, reinterpret_cast<const float*>(u), reinterpret_cast<float*>(x), scratch, sv,
-                                     fa, ev0, ev1, nlaunch);
-        if (h->aux)
-            return launch_rmatvec_mma(h, reinterpret_cast<const float*>(u), reinterpret_cast<float*>(x), scratch, sv,
-                                      fa, ev0, ev1, nlaunch);
+        // FP32: the tensor-core kernel is the only FP32 A^T u (gkl_init fails without it)
+        if (h->tc_state <= 0) return cudaErrorNotSupported;
+        return launch_rmatvec_tc(h, reinterpret_cast<const float*>(u), reinterpret_cast<float*>(x), scratch, sv, fa,
+                                 ev0, ev1, nlaunch);
+    } else {
+        MvPlan p = plan_products(h);
+        T* p1 = static_cast<T*>(scratch);
+        T* p3 = p1 + (size_t)p.tiles * (size_t)h->m;
+        cudaStream_t st = h->stream;
+        dim3 grid((unsigned)p.tiles, (unsigned)p.chunks);
+        if (ev0) cudaEventRecord(ev0, st);
+        k_rmv_part<T><<<grid, kThreads, 0, st>>>(h->packed, h->stride, h->n, p.nwords, h->m, p.rows_per_chunk, u, h->s,
+                                                 p1, p3);
+        if (ev1) cudaEventRecord(ev1, st);
+        if (nlaunch) *nlaunch = 2;
+        FinArgs f{};
+        Sv s{};
+        if (fa) f = *fa;
+        if (sv) s = *sv;
+        k_rmv_fin<T><<<(unsigned)((h->m + kThreads - 1) / kThreads), kThreads, 0, st>>>(p1, p3, p.tiles, h->m, h->mu,
+                                                                                        h->d, h->w, x, f, s);
+        return cudaGetLastError();
     }
-    MvPlan p = plan_products(h);
-    T* p1 = static_cast<T*>(scratch);
-    T* p3 = p1 + (size_t)p.tiles * (size_t)h->m;
-    cudaStream_t st = h->stream;
-    dim3 grid((unsigned)p.tiles, (unsigned)p.chunks);
-    if (ev0) cudaEventRecord(ev0, st);
-    k_rmv_part<T><<<grid, kThreads, 0, st>>>(h->packed, h->stride, h->n, p.nwords, h->m, p.rows_per_chunk, u, h->s, p1,
-                                             p3);
-    if (ev1) cudaEventRecord(ev1, st);
-    if (nlaunch) *nlaunch = 2;
-    FinArgs f{};
-    Sv s{};
-    if (fa) f = *fa;
-    if (sv) s = *sv;
-    k_rmv_fin<T><<<(unsigned)((h->m + kThreads - 1) / kThreads), kThreads, 0, st>>>(p1, p3, p.tiles, h->m, h->mu, h->d,
-                                                                                    h->w, x, f, s);
-    return cudaGetLastError();
 }
 
 template cudaError_t launch_matvec<float>(const gkl_handle*, const float*, float*, void*, const Sv*, const FinArgs*,

@@ -98,6 +98,50 @@ __device__ __forceinline__ void mma_e4m3_ts(uint32_t d, uint32_t a, uint64_t bde
 __device__ __forceinline__ void tc_fence_before() { tc::fence_before(); }
 __device__ __forceinline__ void tc_fence_after() { tc::fence_after(); }
 
+// ---- scale of u~ -------------------------------------------------------------
+
+// Pass 1: max|u~| and sum u~ (FP64), combined by the last block; the scale
+// S = 2^e >= max|u~| and the sum go to dsc[0..2] = {S, 1/S, sum}.
+__global__ void __launch_bounds__(256) k_u_scale(const float* __restrict__ u, const float* __restrict__ s, int64_t n,
+                                                  double* __restrict__ part, unsigned* __restrict__ counter,
+                                                  double* __restrict__ dsc) {
+    double mx = 0.0, sm = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double v = (double)u[i] * (s ? (double)s[i] : 1.0);
+        mx = fmax(mx, fabs(v));
+        sm += v;
+    }
+    __shared__ double smx[32], ssm[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        sm += __shfl_xor_sync(0xffffffffu, sm, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (l == 0) { smx[w] = mx; ssm[w] = sm; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int q = 0; q < nw; ++q) { a = fmax(a, smx[q]); b += ssm[q]; }
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+    if (!arrive_last(counter)) return;
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (unsigned q = 0; q < gridDim.x; ++q) {
+            a = fmax(a, __ldcg(part + 2 * q));
+            b += __ldcg(part + 2 * q + 1);
+        }
+        int e = 0;
+        frexp(a, &e);                              // a = f * 2^e, f in [0.5, 1)
+        double S = a > 0.0 ? ldexp(1.0, e) : 1.0;  // S >= a
+        dsc[0] = S;
+        dsc[1] = 1.0 / S;
+        dsc[2] = b;
+        *counter = 0u;
+    }
+}
+
 // ---- digits of u~ -----------------------------------------------------------
 
 // Position of sample `loc` (0..511) of a stage along the MMA's K axis.  Decode
@@ -523,300 +567,65 @@ __global__ void __launch_bounds__(256) k_miss_gather(const int64_t* __restrict__
     }
 }
 
-// ---- A^T u with the codes on the N side ----------------------------------------
-//
-// The same product in the orientation of the block products: M = 128 rows of
-// which rows 0-6 hold the seven base-16 digits of u~ (the other rows of the
-// digit tiles stay zero), N = 256 SNPs whose codes are decoded by byte permutes
-// into f(code) = g [observed] = 0, 1, 2, 0 in shared memory (128-byte swizzle,
-// K-major), K = samples.  One MMA covers 256 x 32 codes, twice the codes of the
-// N = 16 orientation above at about the same cost per instruction, but it moves
-// 24 KB of shared memory per MMA (the decoded operand written and read, the
-// digit tile read), against 0.5 KB for the N = 16 kernel: measured 116 us per
-// launch at 10,000 x 100,000 against 110 us, so the N = 16 kernel stays the
-// default (GKL_RMV_KERNEL=n256 selects this one).  The digits
-// are those of u~'_i = S 2^-28 X_i, X_i = rint(u~_i 2^28 / S); every
-// accumulator value F_p,j = sum_i f(c_ij) delta_p,i is an exact integer in
-// FP32 (|F_p| <= 32 x 512 x 1023 < 2^24 for K-ranges of at most 1023 stages),
-// and the epilogue recombines z1_j = sum_p 16^(6-p) F_p,j = sum_{i obs} g_ij X_i
-// in 64-bit integers.  Partials: p1[r][j] = S 2^-28 z1_j, p3[r][j] = 0; the
-// missing-code gather adds S 2^-28 sum_{i missing} X_i to p3[0][j] and the
-// finishing kernel forms d_j w_j (sum_r p1 - mu_j (sum_i u~_i - sum_r p3)).
-//
-// Warp roles: 0 copies (two 128-row TMA boxes and four 1 KB digit images per
-// 512-sample stage), 1 issues the MMAs, 2-3 and 5-10 decode (one SNP row per
-// lane), 4 runs the epilogue (tensor-memory lanes 0-31 hold digit rows 0-31).
-namespace {
-constexpr int kN2Rows = 256;                         // SNPs per tile (MMA N)
-constexpr int kN2Box = 2 * kPackedBytes;             // 32 KB: two 128-row boxes of one stage
-constexpr int kN2Tile = 16384;                       // one digit tile: 128 rows x 128 bytes
-constexpr int kN2Img = 1024;                         // rows 0-7 of a digit tile (one 128-sample sub-stage)
-constexpr int kN2RP = 3, kN2RG = 4, kN2RD = 2;       // ring depths: packed stages, digit tiles, decoded tiles
-constexpr int kN2DecWarps = 8;
-constexpr int kN2Threads = 32 * (2 + kN2DecWarps + 1);  // 352
-constexpr int kN2EpiWarp = 4;
-constexpr int kN2MaxRangeStages = 1023;              // 523,776 samples: |F_p| < 2^24
-constexpr uint32_t kN2Lut = 0x00403800u;             // e4m3 bytes of f: 0, 1, 2, 0
-constexpr uint32_t kN2Idesc = tc::idesc_e4m3(256, 0);
-constexpr int kN2Smem = 1024 + kN2RP * kN2Box + kN2RG * kN2Tile + kN2RD * 2 * kN2Tile + 1024;
-static_assert(kN2Smem <= 232448, "shared memory of k_rmv_n256");
-}  // namespace
+// ---- finishing kernel ----------------------------------------------------------
 
-// One block per 128-sample sub-stage: the 1 KB image of digit rows 0-7 (row 7
-// zero) in the swizzled K order of the decode, and X_i into z[] (i < n).
-__global__ void __launch_bounds__(128) k_n2_digits(const float* __restrict__ u, const float* __restrict__ s,
-                                                   int64_t n, const double* __restrict__ dsc,
-                                                   uint8_t* __restrict__ img, int* __restrict__ z) {
-    const int g = blockIdx.x, loc = threadIdx.x;
-    const int64_t i = (int64_t)g * 128 + loc;
-    long long X = 0;
-    if (i < n) X = llrint((double)u[i] * (s ? (double)s[i] : 1.0) * dsc[1] * 268435456.0);  // |X| <= 2^28
-    if (i < n) z[i] = (int)X;
-    int dg[8];
-    dg[7] = 0;
-    for (int p = 6; p >= 1; --p) {
-        const int r = (int)((X + 8) & 15) - 8;
-        dg[p] = r;
-        X = (X - r) >> 4;
+// Final combination over sample blocks (fixed order), then the solver epilogue.
+__global__ void __launch_bounds__(256) k_rmv_tc_fin(const double* __restrict__ p1, const double* __restrict__ p3,
+                                                     int nb, int64_t m, const double* __restrict__ mu,
+                                                     const double* __restrict__ d, const float* __restrict__ w,
+                                                     const double* __restrict__ dsc, float* __restrict__ x, FinArgs fa,
+                                                     Sv sv) {
+    if (fa.role != ROLE_NONE && sv.sc->abort) return;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double sq = 0.0;
+    if (j < m) {
+        double hsum = 0.0, msum = 0.0;
+        for (int b = 0; b < nb; ++b) {
+            hsum += p1[(int64_t)b * m + j];
+            msum += p3[(int64_t)b * m + j];
+        }
+        double dw = d[j];
+        if (w) dw *= (double)w[j];
+        const double obs = dsc[2] - msum;  // sum of u~ over observed samples
+        float val = (float)(dw * (hsum - mu[j] * obs));
+        const float* W = static_cast<const float*>(fa.W);
+        for (int q = 0; q < fa.nsub; ++q) val -= (float)fa.bcol[q] * W[j + (int64_t)q * fa.ldw];
+        x[j] = val;
+        sq = (double)val * (double)val;
     }
-    dg[0] = (int)X;  // in [-16, 16]
-    const int kk = 16 * (loc >> 4) + bt_kpos(loc & 15);
-    uint8_t* t = img + (size_t)g * kN2Img;
-#pragma unroll
-    for (int p = 0; p < 8; ++p)
-        t[bt_swz(p, kk)] = (uint8_t)__nv_cvt_float_to_fp8((float)dg[p], __NV_SATFINITE, __NV_E4M3);
-}
-
-struct N2Args {
-    const uint8_t* img;  // 4 * nstages digit images
-    int nstages, range_stages, nranges, ntiles;
-    int64_t m;
-    const double* dsc;
-    double* p1;
-    double* p3;
-    int* err;
-};
-
-__global__ void __launch_bounds__(kN2Threads, 1) k_rmv_n256(const __grid_constant__ CUtensorMap tmap, N2Args a) {
-    extern __shared__ uint8_t smem_raw[];
-    const uint32_t raw = sm_addr(smem_raw);
-    const uint32_t base = (raw + 1023u) & ~1023u;
-    uint8_t* sb = smem_raw + (base - raw);
-    const uint32_t sP = base, sG = sP + kN2RP * kN2Box, sD = sG + kN2RG * kN2Tile;
-    const uint32_t sBar = sD + kN2RD * 2 * kN2Tile;
-    uint8_t* gP = sb;
-    uint8_t* gG = sb + kN2RP * kN2Box;
-    uint8_t* gD = gG + kN2RG * kN2Tile;
-    auto pfull = [&](int i) { return sBar + 8u * i; };
-    auto pempty = [&](int i) { return sBar + 8u * (kN2RP + i); };
-    auto gfull = [&](int i) { return sBar + 8u * (2 * kN2RP + i); };
-    auto gempty = [&](int i) { return sBar + 8u * (2 * kN2RP + kN2RG + i); };
-    auto dfull = [&](int i) { return sBar + 8u * (2 * kN2RP + 2 * kN2RG + i); };
-    auto dempty = [&](int i) { return sBar + 8u * (2 * kN2RP + 2 * kN2RG + kN2RD + i); };
-    auto afull = [&](int i) { return sBar + 8u * (2 * kN2RP + 2 * kN2RG + 2 * kN2RD + i); };
-    auto aempty = [&](int i) { return sBar + 8u * (2 * kN2RP + 2 * kN2RG + 2 * kN2RD + 2 + i); };
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sb + (sBar - base) + 512);
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // digit rows 8-127 of every ring tile stay zero; the copies write rows 0-7
-    for (int o = 16 * threadIdx.x; o < kN2RG * kN2Tile; o += 16 * kN2Threads)
-        *reinterpret_cast<uint4*>(gG + o) = make_uint4(0u, 0u, 0u, 0u);
-    tc::fence_proxy_async();
-    if (warp == 0) tc::tmem_alloc(sm_addr(tmem_slot), 512);
-    if (threadIdx.x == 32) {
-        for (int i = 0; i < kN2RP; ++i) {
-            bar_init(pfull(i), 1);
-            bar_init(pempty(i), kN2DecWarps);
-        }
-        for (int i = 0; i < kN2RG; ++i) {
-            bar_init(gfull(i), 1);
-            bar_init(gempty(i), 1);
-        }
-        for (int i = 0; i < kN2RD; ++i) {
-            bar_init(dfull(i), kN2DecWarps);
-            bar_init(dempty(i), 1);
-        }
-        for (int i = 0; i < 2; ++i) {
-            bar_init(afull(i), 1);
-            bar_init(aempty(i), 1);
-        }
-        tc::bar_init_fence();
-    }
-    tc::fence_before();
+    if (fa.role == ROLE_NONE) return;
+    __shared__ double s_w[32];
+    double v = warp_sum(sq);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
     __syncthreads();
-    tc::fence_after();
-    const uint32_t tmem = *tmem_slot;
-    const int nitems = a.ntiles * a.nranges;
-    auto fail = [&](int code) { atomicCAS(a.err, 0, code); };
-    auto stages_of = [&](int item, int& k0, int& k1) {
-        const int r = item % a.nranges;
-        k0 = r * a.range_stages;
-        k1 = min(a.nstages, k0 + a.range_stages);
-    };
-
-    if (warp == 0) {
-        // ---- copies: per stage two packed boxes, then its four digit images
-        if (lane == 0) {
-            uint32_t ps = 0, gs = 0;
-            bool ok = true;
-            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-                const int tile = item / a.nranges;
-                int k0, k1;
-                stages_of(item, k0, k1);
-                for (int k = k0; k < k1 && ok; ++k, ++ps) {
-                    const int sp = (int)(ps % kN2RP);
-                    if (!bar_wait(pempty(sp), ((ps / kN2RP) & 1u) ^ 1u)) {
-                        fail(41);
-                        ok = false;
-                        break;
-                    }
-                    bar_expect_tx(pfull(sp), kN2Box);
-                    tma_2d(sP + sp * kN2Box, &tmap, kStageRowBytes * k, kN2Rows * tile, pfull(sp));
-                    tma_2d(sP + sp * kN2Box + kPackedBytes, &tmap, kStageRowBytes * k, kN2Rows * tile + kRows,
-                           pfull(sp));
-                    for (int qq = 0; qq < 4; ++qq, ++gs) {
-                        const int sg = (int)(gs % kN2RG);
-                        if (!bar_wait(gempty(sg), ((gs / kN2RG) & 1u) ^ 1u)) {
-                            fail(42);
-                            ok = false;
-                            break;
-                        }
-                        bar_expect_tx(gfull(sg), kN2Img);
-                        bulk_g2s(sG + sg * kN2Tile, a.img + (size_t)(4 * k + qq) * kN2Img, kN2Img, gfull(sg));
-                    }
-                }
-            }
-            // drain: every issued copy has landed before the CTA may exit
-            for (uint32_t x = ps > (uint32_t)kN2RP ? ps - kN2RP : 0u; x < ps; ++x)
-                if (!bar_wait(pfull((int)(x % kN2RP)), (x / kN2RP) & 1u)) fail(43);
-            for (uint32_t x = gs > (uint32_t)kN2RG ? gs - kN2RG : 0u; x < gs; ++x)
-                if (!bar_wait(gfull((int)(x % kN2RG)), (x / kN2RG) & 1u)) fail(44);
-        }
-    } else if (warp == 1) {
-        // ---- MMA issuer: per 128-sample sub-stage four K-steps of 32 samples
-        if (lane == 0) {
-            uint32_t it = 0, li = 0;
-            bool ok = true;
-            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
-                int k0, k1;
-                stages_of(item, k0, k1);
-                const int nsub = 4 * (k1 - k0);
-                const uint32_t acc = li & 1u;
-                if (!bar_wait(aempty(acc), ((li >> 1) & 1u) ^ 1u)) {
-                    fail(45);
-                    break;
-                }
-                tc::fence_after();
-                const uint32_t dcol = tmem + 256u * acc;
-                for (int g = 0; g < nsub; ++g, ++it) {
-                    const int sg = (int)(it % kN2RG), sd = (int)(it % kN2RD);
-                    if (!bar_wait(gfull(sg), (it / kN2RG) & 1u) || !bar_wait(dfull(sd), (it / kN2RD) & 1u)) {
-                        fail(46);
-                        ok = false;
-                        break;
-                    }
-                    tc::fence_after();
-                    const uint64_t ad = desc_sw128(sG + sg * kN2Tile);
-                    const uint64_t bd = desc_sw128(sD + sd * 2 * kN2Tile);
-#pragma unroll
-                    for (int ks = 0; ks < 4; ++ks) tc::mma_f8_ss(dcol, ad + 2 * ks, bd + 2 * ks, kN2Idesc, (g | ks) != 0);
-                    mma_commit(gempty(sg));
-                    mma_commit(dempty(sd));
-                }
-                if (ok) mma_commit(afull(acc));
-            }
-            if (it > 0) {  // the last commit covers every MMA issued
-                const uint32_t x = it - 1;
-                if (!bar_wait(dempty((int)(x % kN2RD)), (x / kN2RD) & 1u)) fail(47);
-            }
-        }
-    } else if (warp == kN2EpiWarp) {
-        // ---- epilogue: lane p < 7 holds digit row p; 16 x 16 accumulator columns per item
-        const int p = lane & 7;
-        const int sh = lane < 7 ? 4 * (6 - lane) : 0;
-        const double zs = ldexp(a.dsc[0], -28);
-        uint32_t li = 0;
-        for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++li) {
-            const int tile = item / a.nranges, range = item % a.nranges;
-            const uint32_t acc = li & 1u;
-            if (!bar_wait(afull(acc), (li >> 1) & 1u)) {
-                fail(48);
-                break;
-            }
-            tc::fence_after();
-#pragma unroll 1
-            for (int g = 0; g < 16; ++g) {
-                long long zv[16];
-                bt_ld16_scaled(tmem + 256u * acc + 16u * g, sh, zv);
-                if (g == 15) {
-                    tc::fence_before();
-                    __syncwarp();
-                    if (lane == 0) bar_arrive(aempty(acc));
-                }
-                bt_reduce_scatter<8>(zv, p);
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int64_t j = (int64_t)tile * kN2Rows + 16 * g + 2 * p + i;
-                    if (lane < 8 && j < a.m) {
-                        a.p1[(int64_t)range * a.m + j] = zs * (double)zv[i];
-                        a.p3[(int64_t)range * a.m + j] = 0.0;
-                    }
-                }
-            }
-        }
-    } else {
-        // ---- decode: SNP row 32 dw + lane of the tile, one 128-sample sub-stage at a time
-        const int dw = warp < kN2EpiWarp ? warp - 2 : warp - 3;
-        const int row = 32 * dw + lane, box = row >> 7, r7 = row & 7;
-        uint32_t ps = 0, it = 0;
-        bool ok = true;
-        for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-            int k0, k1;
-            stages_of(item, k0, k1);
-            for (int k = k0; k < k1 && ok; ++k, ++ps) {
-                const int sp = (int)(ps % kN2RP);
-                if (!bar_wait(pfull(sp), (ps / kN2RP) & 1u)) {
-                    fail(49);
-                    ok = false;
-                    break;
-                }
-                const uint8_t* src = gP + sp * kN2Box + box * kPackedBytes + (row & 127) * kStageRowBytes;
-                for (int qq = 0; qq < 4; ++qq, ++it) {
-                    const int sd = (int)(it % kN2RD);
-                    const uint4 P0 = *reinterpret_cast<const uint4*>(src + (((2 * qq) ^ r7) << 4));
-                    const uint4 P1 = *reinterpret_cast<const uint4*>(src + (((2 * qq + 1) ^ r7) << 4));
-                    if (!bar_wait(dempty(sd), ((it / kN2RD) & 1u) ^ 1u)) {
-                        fail(50);
-                        ok = false;
-                        break;
-                    }
-                    uint8_t* t = gD + sd * 2 * kN2Tile + (row >> 3) * 1024 + r7 * 128;
-                    const uint32_t Wv[8] = {P0.x, P0.y, P0.z, P0.w, P1.x, P1.y, P1.z, P1.w};
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const uint32_t s0 = Wv[u] & 0x33333333u, s1 = (Wv[u] >> 2) & 0x33333333u;
-                        *reinterpret_cast<uint4*>(t + ((u ^ r7) << 4)) =
-                            make_uint4(__byte_perm(kN2Lut, 0, s0), __byte_perm(kN2Lut, 0, s0 >> 16),
-                                       __byte_perm(kN2Lut, 0, s1), __byte_perm(kN2Lut, 0, s1 >> 16));
-                    }
-                    tc::fence_proxy_async();
-                    __syncwarp();
-                    if (lane == 0) bar_arrive(dfull(sd));
-                }
-                __syncwarp();
-                if (ok && lane == 0) bar_arrive(pempty(sp));
-            }
-        }
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += s_w[q];
+        sv.partials[(int64_t)blockIdx.x * (GKL_MAX_ELL + 2)] = a;
     }
-    tc::fence_before();
+    if (!arrive_last(&sv.sc->counter)) return;
+    __shared__ double s_tot;
+    double tt = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+        tt += __ldcg(sv.partials + (int64_t)b * (GKL_MAX_ELL + 2));
+    tt = warp_sum(tt);
     __syncthreads();
-    if (warp == 0) {
-        tc::fence_after();
-        tc::tmem_dealloc(tmem, 512);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = tt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += s_w[q];
+        s_tot = a;
     }
+    __syncthreads();
+    step_epilogue(sv, fa.role, fa.j, s_tot);
+    __syncthreads();
+    release_counter(&sv.sc->counter);
 }
 
 // ---- host side --------------------------------------------------------------
+
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct TcPlan {
     int nstages, range_stages, nranges, ntiles, grid;
@@ -853,54 +662,17 @@ static TcPlan plan_tc(const gkl_handle* h) {
     return p;
 }
 
-struct N2Plan {
-    int nstages, range_stages, nranges, ntiles, grid;
-    size_t img_bytes, z_bytes, part_bytes;
-};
-
-static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-// Work items (256-SNP tile, K-range) of k_rmv_n256: K-ranges of at most 1023
-// stages; more ranges only where they even out the last wave over the SMs.
-static N2Plan plan_n2(const gkl_handle* h) {
-    N2Plan p;
-    p.nstages = (int)((h->stride + kStageRowBytes - 1) / kStageRowBytes);
-    p.ntiles = (int)((h->m + kN2Rows - 1) / kN2Rows);
-    const int sms = std::max(1, h->num_sms);
-    const int nr0 = (p.nstages + kN2MaxRangeStages - 1) / kN2MaxRangeStages;
-    int best = nr0;
-    double best_eff = 0.0;
-    for (int nr = nr0; nr <= std::min(p.nstages, nr0 + 7); ++nr) {
-        const int rs = (p.nstages + nr - 1) / nr, nranges = (p.nstages + rs - 1) / rs;
-        const double items = (double)p.ntiles * nranges;
-        const double eff = items / (std::ceil(items / sms) * sms);
-        if (eff > best_eff + 0.03) {
-            best_eff = eff;
-            best = nr;
-        }
-    }
-    p.range_stages = (p.nstages + best - 1) / best;
-    p.nranges = (p.nstages + p.range_stages - 1) / p.range_stages;
-    p.grid = (int)std::min<int64_t>((int64_t)p.ntiles * p.nranges, sms);
-    p.img_bytes = (size_t)p.nstages * 4 * kN2Img;
-    p.z_bytes = (size_t)p.nstages * kStageSamples * sizeof(int);
-    p.part_bytes = 2 * (size_t)p.nranges * (size_t)h->m * sizeof(double);
-    return p;
-}
-
 size_t rmv_tc_scratch_bytes(const gkl_handle* h) {
     const TcPlan p = plan_tc(h);
-    const N2Plan q = plan_n2(h);
-    const size_t n16 = p.dig_bytes + al256(p.cs_bytes) + al256(p.z_bytes) + p.part_bytes + 256;
-    const size_t n256 = al256(q.img_bytes) + al256(q.z_bytes) + q.part_bytes + 256;
-    return std::max(n16, n256);
+    return p.dig_bytes + al256(p.cs_bytes) + al256(p.z_bytes) + p.part_bytes + 256;
 }
+
 
 // Prepares the tensor-core path for a handle: the TMA descriptor of the packed
 // matrix (128-byte x 128-row boxes, 128-byte swizzle), the kernel's shared-memory
-// limit and the list of missing codes per SNP.  Returns false (the mma.sync
-// kernel stays in use) if the driver entry point or a step is unavailable or
-// the packed buffer is not 16-byte aligned.
+// limit and the list of missing codes per SNP.  Returns false (gkl_init then
+// fails: the FP32 A^T u has no other kernel) if the driver entry point or a
+// step is unavailable or the packed buffer is not 16-byte aligned.
 bool tc_prepare(gkl_handle* h) {
     if (h->tc_state != 0) return h->tc_state > 0;
     h->tc_state = -1;
@@ -922,8 +694,7 @@ bool tc_prepare(gkl_handle* h) {
     if (r != CUDA_SUCCESS) return false;
     static_assert(sizeof(CUtensorMap) == sizeof(h->tc_map), "tensor map size");
     memcpy(h->tc_map, &map, sizeof(map));
-    if (cudaFuncSetAttribute(k_rmv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess ||
-        cudaFuncSetAttribute(k_rmv_n256, cudaFuncAttributeMaxDynamicSharedMemorySize, kN2Smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_rmv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess)
         return false;
     // list of missing codes per SNP (CSR), built once: counts, host prefix sum, fill
     const int64_t m = h->m;
@@ -954,45 +725,8 @@ bool tc_prepare(gkl_handle* h) {
     return true;
 }
 
-// N = 256 orientation: scale pass, digit images, the MMA kernel, the missing-code
-// gather (p3 only) and the finishing kernel.
-static cudaError_t launch_rmatvec_n256(const gkl_handle* h, const float* u, float* x, void* scratch, const Sv* sv,
-                                       const FinArgs* fa, cudaEvent_t ev0, cudaEvent_t ev1, int* nlaunch) {
-    const N2Plan p = plan_n2(h);
-    uint8_t* img = static_cast<uint8_t*>(scratch);
-    int* z = reinterpret_cast<int*>(img + al256(p.img_bytes));
-    double* p1 = reinterpret_cast<double*>(reinterpret_cast<char*>(z) + al256(p.z_bytes));
-    double* p3 = p1 + (size_t)p.nranges * h->m;
-    double* aux = h->aux;
-    double* dsc = aux;
-    unsigned* counter = reinterpret_cast<unsigned*>(aux + 4);
-    double* part = aux + 8;
-    int* err = reinterpret_cast<int*>(reinterpret_cast<char*>(aux) + kAuxErrOffset);
-    cudaStream_t st = h->stream;
-    const int sblocks = std::min(2 * h->num_sms, (int)((h->n + 255) / 256));
-    k_u_scale<<<std::max(1, sblocks), 256, 0, st>>>(u, h->s, h->n, part, counter, dsc);
-    k_n2_digits<<<4 * p.nstages, 128, 0, st>>>(u, h->s, h->n, dsc, img, z);
-    alignas(64) CUtensorMap map;
-    memcpy(&map, h->tc_map, sizeof(map));
-    N2Args a{img, p.nstages, p.range_stages, p.nranges, p.ntiles, h->m, dsc, p1, p3, err};
-    if (ev0) cudaEventRecord(ev0, st);
-    k_rmv_n256<<<p.grid, kN2Threads, kN2Smem, st>>>(map, a);
-    if (ev1) cudaEventRecord(ev1, st);
-    k_miss_gather<<<(unsigned)((h->m * 8 + 255) / 256), 256, 0, st>>>(h->miss_off, h->miss_idx, h->m, z, dsc, p1,
-                                                                       p3, 0);
-    FinArgs f{};
-    Sv s{};
-    if (fa) f = *fa;
-    if (sv) s = *sv;
-    k_rmv_mma_fin<<<(unsigned)((h->m + 255) / 256), 256, 0, st>>>(p1, p3, p.nranges, h->m, h->mu, h->d, h->w, dsc, x,
-                                                                    f, s);
-    if (nlaunch) *nlaunch = 5;
-    return cudaGetLastError();
-}
-
 cudaError_t launch_rmatvec_tc(const gkl_handle* h, const float* u, float* x, void* scratch, const Sv* sv,
                               const FinArgs* fa, cudaEvent_t ev0, cudaEvent_t ev1, int* nlaunch) {
-    if (h->rmv_n256) return launch_rmatvec_n256(h, u, x, scratch, sv, fa, ev0, ev1, nlaunch);
     const TcPlan p = plan_tc(h);
     uint8_t* dig = static_cast<uint8_t*>(scratch);
     int* cs = reinterpret_cast<int*>(dig + p.dig_bytes);
@@ -1020,7 +754,7 @@ cudaError_t launch_rmatvec_tc(const gkl_handle* h, const float* u, float* x, voi
     Sv s{};
     if (fa) f = *fa;
     if (sv) s = *sv;
-    k_rmv_mma_fin<<<(unsigned)((h->m + 255) / 256), 256, 0, st>>>(p1, p3, p.nranges, h->m, h->mu, h->d, h->w, dsc, x,
+    k_rmv_tc_fin<<<(unsigned)((h->m + 255) / 256), 256, 0, st>>>(p1, p3, p.nranges, h->m, h->mu, h->d, h->w, dsc, x,
                                                                     f, s);
     if (nlaunch) *nlaunch = 5;
     return cudaGetLastError();

@@ -46,20 +46,29 @@ __device__ inline double block_sum_all(double v) {
 //   FILL_DOTS: x = fresh vector; c1 = W^T x
 // W has ncols columns (leading dimension ldw).  Inner products accumulate in
 // FP64; the last block adds the per-block partials in block order.
+//
+// Adaptive second pass (second != null; second[0] = flag, second[1] = count):
+// DOTS also reduces ||x||^2, and its last block asks for the second pass only
+// where the first removes more than half of the squared norm, ||c1||^2 >
+// ||x||^2 / 2 (for an orthonormal W, ||x - W c1||^2 = ||x||^2 - ||c1||^2, so the
+// test is that of Daniel, Gragg, Kaufman and Stewart with eta = 1/sqrt(2)).
+// FILL_DOTS always asks for it.  Without the flag, UPD_DOTS skips the second
+// pass's inner products and UPD_NORM its update.
 template <typename T>
 __global__ void __launch_bounds__(kCgsThreads) k_cgs(Sv sv, int mode, T* __restrict__ x, int64_t len,
                                                     const T* __restrict__ W, int64_t ldw, int ncols,
                                                     const int* __restrict__ cond, int role, int j, uint32_t draw,
-                                                    int64_t chunk) {
+                                                    int64_t chunk, int* second) {
     if (sv.sc->abort) return;
     if (cond && *cond == 0) return;
+    const bool one_pass = second != nullptr && (mode == CGS_UPD_DOTS || mode == CGS_UPD_NORM) && second[0] == 0;
     extern __shared__ unsigned char smem_raw[];
     T* xs = reinterpret_cast<T*>(smem_raw);
     __shared__ double cs[kPartStride];
     const double* cin = nullptr;
     double* cout = nullptr;
-    if (mode == CGS_UPD_DOTS) { cin = sv.coef; cout = sv.coef + kPartStride; }
-    else if (mode == CGS_UPD_NORM) { cin = sv.coef + kPartStride; }
+    if (mode == CGS_UPD_DOTS) { cin = sv.coef; cout = one_pass ? nullptr : sv.coef + kPartStride; }
+    else if (mode == CGS_UPD_NORM) { cin = one_pass ? nullptr : sv.coef + kPartStride; }
     else { cout = sv.coef; }
     if (cin)
         for (int t = threadIdx.x; t < ncols; t += blockDim.x) cs[t] = cin[t];
@@ -80,6 +89,7 @@ __global__ void __launch_bounds__(kCgsThreads) k_cgs(Sv sv, int mode, T* __restr
         xs[i - r0] = xi;
         sq += (double)xi * (double)xi;
     }
+    if (mode == CGS_UPD_DOTS && one_pass) return;  // the update alone: no inner products needed
     __syncthreads();
     double* part = sv.partials + (int64_t)blockIdx.x * kPartStride;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -100,6 +110,10 @@ __global__ void __launch_bounds__(kCgsThreads) k_cgs(Sv sv, int mode, T* __restr
             double acc = warp_sum((double)acc_w);
             if (lane == 0) part[k] = acc;
         }
+        if (second && (mode == CGS_DOTS || mode == CGS_FILL_DOTS)) {
+            const double t = block_sum_all(sq);
+            if (threadIdx.x == 0) part[ncols] = t;
+        }
     }
     if (!arrive_last(&sv.sc->counter)) return;
     const int nb = gridDim.x;
@@ -115,6 +129,18 @@ __global__ void __launch_bounds__(kCgsThreads) k_cgs(Sv sv, int mode, T* __restr
             v = warp_sum(v);
             if (lane == 0) cout[k] = v;
         }
+        if (second && (mode == CGS_DOTS || mode == CGS_FILL_DOTS)) {
+            double v = 0.0;
+            for (int b = threadIdx.x; b < nb; b += blockDim.x) v += __ldcg(sv.partials + (int64_t)b * kPartStride + ncols);
+            const double x2 = block_sum_all(v);  // also orders the cout writes above before the read below
+            if (threadIdx.x == 0) {
+                double cc = 0.0;
+                for (int k = 0; k < ncols; ++k) cc += cout[k] * cout[k];
+                const int again = mode == CGS_FILL_DOTS || !(cc <= 0.5 * x2);
+                second[0] = again;
+                second[1] += again;
+            }
+        }
     }
     __syncthreads();
     release_counter(&sv.sc->counter);
@@ -122,7 +148,7 @@ __global__ void __launch_bounds__(kCgsThreads) k_cgs(Sv sv, int mode, T* __restr
 
 template <typename T>
 cudaError_t launch_cgs(const Sv& sv, cudaStream_t st, int mode, T* x, int64_t len, const T* W, int64_t ldw, int ncols,
-                       const int* cond, int role, int j, uint32_t draw, int num_sms) {
+                       const int* cond, int role, int j, uint32_t draw, int num_sms, int* second) {
     int grid = cgs_grid(len, num_sms);
     int64_t chunk = (len + grid - 1) / grid;
     size_t smem = (size_t)chunk * sizeof(T);
@@ -135,7 +161,7 @@ cudaError_t launch_cgs(const Sv& sv, cudaStream_t st, int mode, T* x, int64_t le
         }
         if (smem > 200 * 1024) return cudaErrorInvalidValue;
     }
-    k_cgs<T><<<grid, kCgsThreads, smem, st>>>(sv, mode, x, len, W, ldw, ncols, cond, role, j, draw, chunk);
+    k_cgs<T><<<grid, kCgsThreads, smem, st>>>(sv, mode, x, len, W, ldw, ncols, cond, role, j, draw, chunk, second);
     return cudaGetLastError();
 }
 
@@ -293,7 +319,27 @@ __global__ void k_init_state(Sv sv) {
         sc->svd_fallback = 0;
         sc->n_svd_fallback = 0;
         sc->n_svd_cluster = 0;
+        sc->second_u[0] = sc->second_u[1] = 0;
+        sc->second_v[0] = sc->second_v[1] = 0;
     }
+}
+
+// PC scores S = U diag(sigma): S[i + n c] = U[i + n c] sigma_c.
+template <typename T>
+__global__ void k_scores(const T* __restrict__ U, const double* __restrict__ sigma, int64_t n, int k,
+                         T* __restrict__ S) {
+    const int64_t tot = n * k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x)
+        S[e] = (T)((double)U[e] * sigma[e / n]);
+}
+
+cudaError_t launch_scores(cudaStream_t st, int prec, const void* U, const double* sigma, int64_t n, int k, void* S) {
+    const unsigned grid = (unsigned)std::min<int64_t>((n * k + 255) / 256, 4096);
+    if (prec == GKL_FP64)
+        k_scores<double><<<grid, 256, 0, st>>>(static_cast<const double*>(U), sigma, n, k, static_cast<double*>(S));
+    else
+        k_scores<float><<<grid, 256, 0, st>>>(static_cast<const float*>(U), sigma, n, k, static_cast<float*>(S));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_init_state(const Sv& sv, cudaStream_t st) {
@@ -302,9 +348,9 @@ cudaError_t launch_init_state(const Sv& sv, cudaStream_t st) {
 }
 
 template cudaError_t launch_cgs<float>(const Sv&, cudaStream_t, int, float*, int64_t, const float*, int64_t, int,
-                                       const int*, int, int, uint32_t, int);
+                                       const int*, int, int, uint32_t, int, int*);
 template cudaError_t launch_cgs<double>(const Sv&, cudaStream_t, int, double*, int64_t, const double*, int64_t, int,
-                                        const int*, int, int, uint32_t, int);
+                                        const int*, int, int, uint32_t, int, int*);
 template cudaError_t launch_scale<float>(const Sv&, cudaStream_t, float*, int64_t, const double*);
 template cudaError_t launch_scale<double>(const Sv&, cudaStream_t, double*, int64_t, const double*);
 template cudaError_t launch_fill_random<float>(const Sv&, cudaStream_t, float*, int64_t, uint32_t, int);

@@ -17,16 +17,16 @@ import torch
 from .build import LIB as _LIB_PATH
 
 FP64, FP32, BLOCK, BLOCK16 = 0, 1, 2, 3
-REORTH_FULL, REORTH_PARTIAL = 0, 1
-OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, NOT_CONVERGED, ERR_GAP, ERR_STATE = range(7)
+REORTH_FULL, REORTH_PARTIAL, REORTH_DGKS, REORTH_ONESIDED = 0, 1, 2, 3
+OK, ERR_ARG, ERR_CUDA, ERR_NONFINITE, NOT_CONVERGED, ERR_GAP, ERR_STATE, RANK_DEFICIENT = range(8)
 
 _PREC = {"fp64": FP64, "fp32": FP32, "block": BLOCK, "block16": BLOCK16}
-_REORTH = {"full": REORTH_FULL, "partial": REORTH_PARTIAL}
+_REORTH = {"full": REORTH_FULL, "partial": REORTH_PARTIAL, "dgks": REORTH_DGKS, "onesided": REORTH_ONESIDED}
 _DTYPE = {FP64: torch.float64, FP32: torch.float32, BLOCK: torch.float32, BLOCK16: torch.float32}
 
 EXPORTS = ["gkl_version", "gkl_last_error", "gkl_opts_default", "gkl_colstats", "gkl_init", "gkl_set_stream",
            "gkl_set_weights", "gkl_matvec", "gkl_rmatvec", "gkl_svd", "gkl_destroy", "gkl_matvec_noalloc",
-           "gkl_grad", "gkl_matmat"]
+           "gkl_grad", "gkl_matmat", "gkl_scores", "gkl_sync"]
 
 
 class GKLError(RuntimeError):
@@ -38,8 +38,9 @@ class GKLError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("ell", ctypes.c_int32), ("k_keep", ctypes.c_int32),
                 ("reorth", ctypes.c_int32), ("precision", ctypes.c_int32), ("maxit", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("block", ctypes.c_int32), ("tol", ctypes.c_double), ("omega", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("v0", ctypes.c_void_p)]
+                ("profile", ctypes.c_int32), ("block", ctypes.c_int32), ("out_host", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("tol", ctypes.c_double), ("omega", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("v0", ctypes.c_void_p)]
 
 
 class Info(ctypes.Structure):
@@ -49,8 +50,8 @@ class Info(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("launches", ctypes.c_int64), ("n_mv", ctypes.c_int64),
                 ("n_rmv", ctypes.c_int64), ("ms_mv", ctypes.c_double), ("ms_rmv", ctypes.c_double),
                 ("jacobi_sweeps", ctypes.c_int32), ("svd_fallbacks", ctypes.c_int32),
-                ("svd_clusters", ctypes.c_int32), ("reserved", ctypes.c_int32), ("ms_svd", ctypes.c_double),
-                ("ms_cgs", ctypes.c_double)]
+                ("svd_clusters", ctypes.c_int32), ("rank", ctypes.c_int32), ("ms_svd", ctypes.c_double),
+                ("ms_cgs", ctypes.c_double), ("second_u", ctypes.c_int32), ("second_v", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -84,8 +85,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.gkl_grad.restype = ctypes.c_int
     lib.gkl_matmat.argtypes = [vp, i32, i32, i32, vp, i64, vp, i64]
     lib.gkl_matmat.restype = ctypes.c_int
+    lib.gkl_scores.argtypes = [vp, vp, i32]
+    lib.gkl_sync.argtypes = [vp]
     for f in ("gkl_colstats", "gkl_init", "gkl_set_stream", "gkl_set_weights", "gkl_matvec", "gkl_rmatvec",
-              "gkl_svd", "gkl_destroy", "gkl_matvec_noalloc"):
+              "gkl_svd", "gkl_destroy", "gkl_matvec_noalloc", "gkl_scores", "gkl_sync"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -135,7 +138,7 @@ class SVDResult:
 
     @property
     def converged(self) -> bool:
-        return self.status == OK
+        return self.status in (OK, RANK_DEFICIENT)
 
 
 class GKL:
@@ -157,6 +160,10 @@ class GKL:
                                   _stream()))
         self._h = h
         self._weights = (None, None)
+        # bumped by every solve and weight change: a backward pass checks that the
+        # handle still holds the triplets its forward pass produced
+        self.generation = 0
+        self._last = (0, torch.float64)  # k and dtype of the last solve
 
     def close(self):
         if getattr(self, "_h", None):
@@ -176,6 +183,7 @@ class GKL:
         self._sync_stream()
         s = None if s is None else s.to(self.device, torch.float32).contiguous()
         w = None if w is None else w.to(self.device, torch.float32).contiguous()
+        self.generation += 1
         _check(lib().gkl_set_weights(self._h, _ptr(s), _ptr(w)), self._h)
         self._weights = (s, w)
 
@@ -209,42 +217,73 @@ class GKL:
         _check(lib().gkl_matmat(self._h, int(transpose), q, digits, _ptr(X), rows_in, _ptr(Y), rows_out), self._h)
         return Y
 
-    def svd(self, k: int, ell: int, reorth: str = "full", precision: str = "fp64", tol: float = 1e-10,
+    def svd(self, k: int, ell: int, reorth: str = "dgks", precision: str = "fp64", tol: float = 1e-10,
             maxit: int = 1000, k_keep: int = 0, omega: float = 0.0, seed: int = 1,
             v0: torch.Tensor | None = None, want_u: bool = True, want_v: bool = True, profile: bool = False,
             U: torch.Tensor | None = None, V: torch.Tensor | None = None, raise_on_fail: bool = True,
-            block: int = 0) -> SVDResult:
+            block: int = 0, out_host: bool = False) -> SVDResult:
+        """Top-k triplets.  U and V come back as n x k and m x k views of
+        column-major buffers, on the device, or in pinned host memory with
+        out_host=True (the library copies them there)."""
         prec = _PREC[precision]
         dt = _DTYPE[prec]
         o = Opts()
         lib().gkl_opts_default(ctypes.byref(o))
         o.k, o.ell, o.k_keep, o.reorth, o.precision, o.maxit = k, ell, k_keep, _REORTH[reorth], prec, maxit
         o.tol, o.omega, o.seed, o.profile = tol, omega, seed, int(profile)
-        o.block = block
+        o.block, o.out_host = block, int(out_host)
         if v0 is not None:
             v0 = v0.to(self.device, dt).contiguous()
             o.v0 = v0.data_ptr()
+        where = dict(device="cpu", pin_memory=True) if out_host else dict(device=self.device)
         if U is None and want_u:
-            U = torch.empty((k, self.n), dtype=dt, device=self.device)  # column-major n x k
+            U = torch.empty((k, self.n), dtype=dt, **where)  # column-major n x k
         if V is None and want_v:
-            V = torch.empty((k, self.m), dtype=dt, device=self.device)
+            V = torch.empty((k, self.m), dtype=dt, **where)
         sigma = np.zeros(k)
         resid = np.zeros(k)
         info = Info()
         self._sync_stream()
+        self.generation += 1
         st = lib().gkl_svd(self._h, ctypes.byref(o), sigma.ctypes.data_as(ctypes.c_void_p), _ptr(U), _ptr(V),
                            resid.ctypes.data_as(ctypes.c_void_p), ctypes.byref(info))
-        if st not in (OK, NOT_CONVERGED) and raise_on_fail:
+        if st not in (OK, NOT_CONVERGED, RANK_DEFICIENT) and raise_on_fail:
             _check(st, self._h)
+        self._last = (k, dt)
         return SVDResult(sigma, None if U is None else U.T, None if V is None else V.T, resid, info.as_dict(), st)
 
+    def scores(self, out_host: bool = False) -> torch.Tensor:
+        """PC scores U diag(sigma) of the last successful solve (n x k view of a
+        column-major buffer), computed by the library."""
+        k = self._last_k()
+        dt = self._last_dtype
+        where = dict(device="cpu", pin_memory=True) if out_host else dict(device=self.device)
+        S = torch.empty((k, self.n), dtype=dt, **where)
+        self._sync_stream()
+        _check(lib().gkl_scores(self._h, _ptr(S), int(out_host)), self._h)
+        return S.T
+
+    def sync(self):
+        """Synchronise the handle's stream; raises if a tensor-core product's
+        bounded wait ran out since the last check."""
+        _check(lib().gkl_sync(self._h), self._h)
+
+    def _last_k(self):
+        return self._last[0]
+
+    @property
+    def _last_dtype(self):
+        return self._last[1]
+
     def grad(self, sigma_bar=None, scores_bar: torch.Tensor | None = None, want_w: bool = True,
-             want_s: bool = True, min_relgap: float = 1e-3, dtype=torch.float64):
+             want_s: bool = True, min_relgap: float = 1e-3, dtype=None):
         """(dL/ds, dL/dw) for the triplets of the last converged svd() call.
 
         sigma_bar: k adjoints of the singular values; scores_bar: n x k
-        adjoints of the PC scores U diag(sigma).  dtype must be the precision
-        of that solve."""
+        adjoints of the PC scores U diag(sigma).  dtype: the precision of that
+        solve (float64 after "fp64", float32 otherwise; None = as it was)."""
+        if dtype is None:
+            dtype = self._last_dtype
         sb = None
         if sigma_bar is not None:
             sb = np.ascontiguousarray(np.asarray(sigma_bar, dtype=np.float64))
@@ -274,14 +313,18 @@ class GKLFunction(torch.autograd.Function):
         if not r.converged:
             raise GKLError(NOT_CONVERGED, "forward solve did not converge")
         ctx.handle, ctx.min_relgap = handle, min_relgap
+        ctx.generation = handle.generation
         ctx.dtype = r.U.dtype
         ctx.sdtype, ctx.wdtype = s.dtype, w.dtype
         sigma = torch.tensor(r.sigma, dtype=torch.float64, device=r.U.device)
-        scores = r.U * sigma.to(r.U.dtype)[None, :]
+        scores = handle.scores()
         return sigma, scores
 
     @staticmethod
     def backward(ctx, sigma_bar, scores_bar):
+        if ctx.handle.generation != ctx.generation:
+            raise GKLError(ERR_STATE, "the handle was solved again or its weights changed after this forward pass; "
+                                      "its stored triplets no longer belong to this graph")
         sb = None if sigma_bar is None else sigma_bar.detach().double().cpu().numpy()
         gs, gw = ctx.handle.grad(sb, scores_bar, min_relgap=ctx.min_relgap, dtype=ctx.dtype)
         return gs.to(ctx.sdtype), gw.to(ctx.wdtype), None, None, None

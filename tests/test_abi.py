@@ -48,7 +48,8 @@ def test_host_only_entry_points(lib):
     assert b"sm_103a" in lib.gkl_version()
     o = gkl.Opts()
     lib.gkl_opts_default(ctypes.byref(o))
-    assert (o.k, o.ell, o.reorth, o.precision, o.maxit) == (10, 30, 0, 0, 1000)
+    assert (o.k, o.ell, o.reorth, o.precision, o.maxit) == (10, 30, gkl.REORTH_DGKS, 0, 1000)
+    assert (o.out_host, o.reserved0, o.block) == (0, 0, 0)
     assert o.tol == 1e-10 and o.v0 is None
     assert lib.gkl_last_error(None)
 
@@ -64,3 +65,36 @@ def test_argument_errors_without_device(lib):
     assert lib.gkl_init(ctypes.byref(h), fake, 100, 10, 16, None, None, None) == gkl.ERR_ARG  # 16*4 < 100
     assert lib.gkl_svd(None, None, None, None, None, None, None) == gkl.ERR_ARG
     assert lib.gkl_matvec(None, 0, None, None) == gkl.ERR_ARG
+    assert lib.gkl_scores(None, None, 0) == gkl.ERR_ARG
+    assert lib.gkl_sync(None) == gkl.ERR_ARG
+    assert lib.gkl_grad(None, None, None, None, None, 0.0) == gkl.ERR_ARG
+
+
+def test_struct_layouts_match_header():
+    """The ctypes mirrors of gkl_opts and gkl_info have the C layout: field
+    offsets as a C compiler lays out include/gkl.h (checked with gcc)."""
+    import shutil
+    import subprocess
+    import tempfile
+    from paper_1808_03374_gb300 import gkl
+    gcc = shutil.which("gcc")
+    if not gcc:
+        pytest.skip("gcc not found")
+    fields = {"gkl_opts": gkl.Opts, "gkl_info": gkl.Info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gkl.h"', "int main(void) {"]
+    for cname, cls in fields.items():
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "layout.c")
+        open(src, "w").write("\n".join(lines))
+        exe = os.path.join(d, "layout")
+        subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = dict(line.rsplit(" ", 1) for line in out if line)
+    for cname, cls in fields.items():
+        assert int(got[cname]) == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(cls, f).offset, (cname, f)

@@ -113,3 +113,47 @@ def test_gap_and_state_errors(gk):
     with pytest.raises(gk.GKLError) as e:
         h.grad(None, Sbar, min_relgap=0.5)
     assert e.value.code == gk.ERR_GAP
+
+
+def test_weight_change_and_resolve_invalidate_triplets(gk):
+    """gkl_set_weights changes the operator: the stored triplets no longer
+    serve gkl_grad (GKL_ERR_STATE) until the next solve; an autograd backward
+    whose handle was solved again after its forward pass refuses too."""
+    import torch
+    g, s, w, c, r = problem(150, 900, 3, 35, 6)
+    h = gk.GKL(to_dev(g.packed), 150)
+    res = h.svd(k=6, ell=24, precision="fp64", tol=1e-12)
+    assert res.converged
+    h.grad(np.ones(6), want_s=False)
+    h.set_weights(torch.tensor(s, dtype=torch.float32), torch.tensor(w, dtype=torch.float32))
+    with pytest.raises(gk.GKLError) as e:
+        h.grad(np.ones(6), want_s=False)
+    assert e.value.code == gk.ERR_STATE
+    with pytest.raises(gk.GKLError) as e:
+        h.scores()
+    assert e.value.code == gk.ERR_STATE
+    st = torch.tensor(s, dtype=torch.float64, requires_grad=True)
+    wt = torch.tensor(w, dtype=torch.float64, requires_grad=True)
+    kw = dict(k=6, ell=24, precision="fp64", tol=1e-12)
+    sigma, scores = gk.GKLFunction.apply(st, wt, h, kw, 1e-3)
+    h.svd(**kw)  # the handle now holds another solve's triplets
+    with pytest.raises(gk.GKLError) as e:
+        (sigma ** 2).sum().backward()
+    assert e.value.code == gk.ERR_STATE
+
+
+def test_sigma_gradient_after_block_solve(gk):
+    """The block form leaves its (FP32) triplets in the handle: the sigma part
+    of the gradient equals its closed form 2 sum_i sigma_i^2 v_ij^2 / w_j."""
+    import torch
+    g, s, w, c, r = problem(700, 4000, 3, 36, 6)
+    h = gk.GKL(to_dev(g.packed), 700)
+    h.set_weights(None, torch.tensor(w, dtype=torch.float32))
+    res = h.svd(k=6, ell=48, precision="block", block=8, tol=1e-6, seed=2)
+    assert res.converged
+    _, gw = h.grad(2.0 * res.sigma, want_s=False)
+    assert gw.dtype == torch.float32
+    V = res.V.double().cpu().numpy()
+    closed = 2.0 * (V ** 2) @ (res.sigma ** 2) / w.astype(np.float32).astype(np.float64)
+    err = np.abs(gw.double().cpu().numpy() - closed).max() / np.abs(closed).max()
+    assert err < 1e-4, err

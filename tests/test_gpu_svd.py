@@ -1,7 +1,7 @@
 """GPU parity of the thick-restarted GKL solver against the FP64 CPU oracle.
 
-Bars (relative to sigma_1 where absolute): FP64 path, singular values to 1e-10
-relative; FP32 path, 1e-5 relative.  Singular vectors are compared through
+Bars: FP64 path, every singular value to 1e-10 of itself (relative); FP32
+path, 1e-5 relative.  Singular vectors are compared through
 the angle to the oracle's vector, bounded by (residual + rounding)/gap, since
 a vector's error is its residual divided by the gap to the rest of the
 spectrum (section 3, refined bounds).
@@ -61,7 +61,7 @@ def check_against_oracle(M, ref, r, k, sig_rel, vec_eps, omega=0.0):
     so the true residual may exceed it by up to omega * sigma_1."""
     assert r.converged, r.info
     assert np.all(np.diff(r.sigma) <= 0)
-    rel = np.abs(r.sigma - ref.sigma[:k]) / ref.sigma[0]
+    rel = np.abs(r.sigma - ref.sigma[:k]) / ref.sigma[:k]
     assert rel.max() < sig_rel, (rel.max(), r.sigma[:3], ref.sigma[:3])
     U = r.U.double().cpu().numpy()
     V = r.V.double().cpu().numpy()
@@ -87,7 +87,7 @@ def test_fp64_full_two_population_workload(gk):
     assert r.info["max_rel_resid"] <= w.tol
 
 
-@pytest.mark.parametrize("reorth", ["full", "partial"])
+@pytest.mark.parametrize("reorth", ["full", "partial", "dgks", "onesided"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_admixture_small(gk, precision, reorth):
     g = small_geno(2003, 15_007, pops=5, miss=0.02, seed=41)
@@ -95,10 +95,21 @@ def test_admixture_small(gk, precision, reorth):
     M, ref, r = run_pair(gk, g, 10, 28, tol, precision, reorth)
     sig_rel = 1e-10 if precision == "fp64" else 1e-5
     vec_eps = 1e-13 if precision == "fp64" else 3e-6
-    omega = 0.0 if reorth == "full" else (1e-8 if precision == "fp64" else 2.0 ** -12)
+    omega = 0.0 if reorth in ("full", "dgks") else (1e-8 if precision == "fp64" else 2.0 ** -12)
     check_against_oracle(M, ref, r, 10, sig_rel, vec_eps, omega)
+    i = r.info
     if reorth == "partial":
-        assert r.info["reorth_u"] < r.info["matvec_pairs"]
+        assert i["reorth_u"] < i["matvec_pairs"]
+    if reorth in ("full", "partial"):
+        assert i["second_u"] == 0 and i["second_v"] == 0  # both passes always run, uncounted
+    if reorth == "dgks":
+        # every step reorthogonalises, and the first pass almost always suffices
+        assert i["reorth_v"] == i["matvec_pairs"]
+        assert i["second_u"] < i["reorth_u"] // 2 and i["second_v"] < i["reorth_v"] // 2
+    if reorth == "onesided":
+        # n < m: u (the shorter side) every step, v only when its estimate asks
+        assert i["reorth_u"] >= i["matvec_pairs"] - i["cycles"]
+        assert i["reorth_v"] < i["matvec_pairs"]
 
 
 def test_tiny_ragged_and_k1(gk):
@@ -122,6 +133,59 @@ def test_breakdown_on_duplicated_samples(gk):
     r = h.svd(k=8, ell=45, tol=1e-12, precision="fp64", v0=torch.tensor(synth.normal_vec(2, 0, m)))
     assert r.converged and r.info["breakdowns"] > 0
     assert np.allclose(r.sigma, sd[:8], rtol=1e-10)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_rank_deficient_status(gk, precision):
+    """8 distinct samples, each twice: centred, the rank is at most 7.  Asking
+    for k = 10 returns GKL_RANK_DEFICIENT with the 7 nonzero values of the
+    dense SVD and exact zeros after them."""
+    import torch
+    from tests.test_oracle_core import pack_codes
+    n0, m = 8, 400
+    g = synth.genotypes(synth.GenoSpec(n=n0, m=m, n_pops=2, miss_rate=0.0, seed=31))
+    codes = np.stack([(g.packed >> (2 * t)) & 3 for t in range(4)], -1).reshape(m, -1)[:, :n0]
+    packed = pack_codes(np.concatenate([codes, codes], axis=1))
+    M = oracle.Matrix.from_packed(packed, 2 * n0)
+    sd = np.linalg.svd(M.dense(), compute_uv=False)
+    rank = int(np.sum(sd > 1e-10 * sd[0]))
+    assert rank <= 7
+    h = gk.GKL(to_dev(packed), 2 * n0)
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    r = h.svd(k=10, ell=14, tol=tol, precision=precision, maxit=200)
+    assert r.status == gk.RANK_DEFICIENT and r.converged
+    assert r.info["rank"] == rank
+    assert np.all(r.sigma[rank:] == 0.0)
+    rel = np.abs(r.sigma[:rank] - sd[:rank]) / sd[:rank]
+    assert rel.max() < (1e-10 if precision == "fp64" else 1e-5)
+
+
+def test_host_outputs_scores_and_sync(gk):
+    """out_host=True copies U and V into host memory (same values as the
+    device outputs); gkl_scores gives U diag(sigma); gkl_sync reports no
+    pending error; a host pointer without out_host is rejected."""
+    import torch
+    g = small_geno(900, 5000, pops=3, seed=12)
+    h = gk.GKL(to_dev(g.packed), g.n)
+    for prec in ("fp64", "fp32", "block"):
+        kw = dict(k=5, ell=24 if prec != "block" else 48, precision=prec, tol=1e-6, seed=4)
+        if prec == "block":
+            kw["block"] = 8
+        rd = h.svd(**kw)
+        rh = h.svd(out_host=True, **kw)
+        assert not rh.U.is_cuda and not rh.V.is_cuda
+        assert np.array_equal(rd.sigma, rh.sigma)
+        assert bool((rd.U.cpu() == rh.U).all()) and bool((rd.V.cpu() == rh.V).all())
+        S = h.scores()
+        expect = rh.U.double() * torch.tensor(rh.sigma)[None, :]
+        assert torch.allclose(S.double().cpu(), expect, rtol=1e-6 if prec != "fp64" else 1e-15, atol=0)
+        Sh = h.scores(out_host=True)
+        assert bool((Sh == S.cpu()).all())
+    h.sync()
+    with pytest.raises(gk.GKLError) as e:
+        bad = torch.empty(5, g.n, dtype=torch.float64)  # host memory without out_host
+        h.svd(k=5, ell=24, precision="fp64", U=bad)
+    assert e.value.code == gk.ERR_ARG
 
 
 def test_not_converged_and_argument_errors(gk):

@@ -1,15 +1,12 @@
 """tcgen05 A^T u (FP32 path) against the FP64 oracle, elementwise.
 
-Two kernels: the default one with N = 16 (k_rmv_tc) and the one with 256
-SNPs on the MMA's N side (k_rmv_n256, GKL_RMV_KERNEL=n256).  Both compute
-sum_i g_ij u~'_i exactly, where u~' is u~ = s o u truncated
-to 28 fractional bits of S = 2^e >= max|u~| (max|u~| = f 2^e, f in [1/2, 1)) (|u~ - u~'| <= 2^-29 S), and
-rounds once to FP32 at the end.  Bound per entry:
+The kernel computes sum_i g_ij u~'_i exactly, where u~' is u~ = s o u
+written in fixed point relative to S = 2^e >= max|u~| (max|u~| = f 2^e, f in
+[1/2, 1)) with |u~ - u~'| <= 2^-29 S, and rounds once to FP32 at the end.
+Bound per entry:
     |x_j - xo_j| <= 2^-23 |xo_j| + 2^-28 n S d_j w_j
 (the second term covers the truncation: |g - mu| <= 2 per entry).
 """
-import os
-
 import numpy as np
 import pytest
 
@@ -18,10 +15,8 @@ from tests.helpers import oracle_matrix, small_geno, to_dev
 
 pytestmark = pytest.mark.gpu
 
-# ragged tails in both directions; n = 70,000 spans two K-ranges of the N = 16
-# kernel, n = 600,000 two of the N = 256 kernel (1023 stages of 512 samples each)
-SHAPES = [(1, 1), (5, 3), (255, 129), (256, 128), (257, 300), (1000, 2000), (4099, 777), (70_000, 300),
-          (600_000, 130)]
+# ragged tails in both directions; n = 70,000 spans two K-ranges of the kernel
+SHAPES = [(1, 1), (5, 3), (255, 129), (256, 128), (257, 300), (1000, 2000), (4099, 777), (70_000, 300)]
 
 
 @pytest.fixture(scope="module")
@@ -32,18 +27,8 @@ def gk():
     return gkl
 
 
-def handle(gk, g, kernel="tc"):
-    old = os.environ.get("GKL_RMV_KERNEL")
-    if kernel:
-        os.environ["GKL_RMV_KERNEL"] = kernel
-    try:
-        return gk.GKL(to_dev(g.packed), g.n)
-    finally:
-        if kernel:
-            if old is None:
-                del os.environ["GKL_RMV_KERNEL"]
-            else:
-                os.environ["GKL_RMV_KERNEL"] = old
+def handle(gk, g):
+    return gk.GKL(to_dev(g.packed), g.n)
 
 
 def bound(M, ut, xo):
@@ -54,16 +39,13 @@ def bound(M, ut, xo):
 
 @pytest.mark.parametrize("n,m", SHAPES)
 @pytest.mark.parametrize("weights", [False, True])
-@pytest.mark.parametrize("kernel", ["tc", "n256"])
-def test_tc_rmatvec_elementwise(gk, n, m, weights, kernel):
+def test_tc_rmatvec_elementwise(gk, n, m, weights):
     import torch
-    if n == 600_000 and (weights or kernel == "tc"):
-        pytest.skip("one large case: the N = 256 kernel's second K-range")
     g = small_geno(n, m, miss=0.03, seed=5 * n + m)
     s = synth.uniform_vec(13, 0, n, 0.5, 1.5).astype(np.float32).astype(np.float64) if weights else None
     w = synth.uniform_vec(13, 1, m, 0.5, 1.5).astype(np.float32).astype(np.float64) if weights else None
     M = oracle_matrix(g, s, w)
-    h = handle(gk, g, kernel)
+    h = handle(gk, g)
     if weights:
         h.set_weights(torch.tensor(s, dtype=torch.float32), torch.tensor(w, dtype=torch.float32))
     u = synth.normal_vec(17, n, n).astype(np.float32)
@@ -74,20 +56,31 @@ def test_tc_rmatvec_elementwise(gk, n, m, weights, kernel):
     assert np.all(np.abs(x - xo) <= bound(M, ut, xo))
 
 
-def test_tc_agrees_with_mma_kernel(gk):
+def test_tc_all_missing_and_monomorphic_rows(gk):
+    """Rows that are entirely missing, entirely one code, or one observed entry:
+    the centring and the missing-code terms must cancel exactly to 0 where the
+    oracle gives 0."""
     import torch
-    n, m = 3001, 2049
-    g = small_geno(n, m, miss=0.02, seed=77)
-    M = oracle_matrix(g)
-    u = torch.tensor(synth.normal_vec(19, 0, n).astype(np.float32), device="cuda")
-    x_tc = handle(gk, g).rmatvec(u).double().cpu().numpy()
-    x_256 = handle(gk, g, "n256").rmatvec(u).double().cpu().numpy()
-    x_mma = handle(gk, g, "mma").rmatvec(u).double().cpu().numpy()
-    xo = M.rmatvec(u.double().cpu().numpy())
-    b = bound(M, u.double().cpu().numpy(), xo)
-    assert np.all(np.abs(x_tc - xo) <= b)
-    assert np.all(np.abs(x_256 - xo) <= b)
-    assert np.all(np.abs(x_mma - xo) <= 2 * b)
+    n, m = 2051, 260
+    g = small_geno(n, m, miss=0.02, seed=41)
+    packed = g.packed.copy()
+    packed[0, :] = 0xFF                       # all missing (and padding)
+    packed[1, : (n + 3) // 4] = 0x55          # all code 1: monomorphic, d = 0
+    packed[2, :] = 0xFF
+    packed[2, 0] = 0xFC                       # one observed entry (sample 0, code 0)
+    packed[3, : (n + 3) // 4] = 0xAA          # all code 2
+    for r in (1, 3):                          # padding entries of the last byte hold code 3
+        tail = n % 4
+        if tail:
+            packed[r, n // 4] = (packed[r, n // 4] & ((1 << (2 * tail)) - 1)) | (0xFF << (2 * tail) & 0xFF)
+    h = gk.GKL(to_dev(packed), n)
+    from oracle import Matrix
+    M = Matrix.from_packed(packed, n)
+    u = synth.normal_vec(29, 0, n).astype(np.float32)
+    x = h.rmatvec(torch.tensor(u, device="cuda")).double().cpu().numpy()
+    xo = M.rmatvec(u.astype(np.float64))
+    assert np.all(x[:4] == 0.0) and np.all(xo[:4] == 0.0)
+    assert np.all(np.abs(x - xo) <= bound(M, u.astype(np.float64), xo))
 
 
 def test_tc_special_vectors(gk):

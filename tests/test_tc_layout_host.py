@@ -4,9 +4,14 @@ CPU (no GPU needed):
 
 - bt_kpos maps the 16 samples of a code word onto K positions 0..15 one to one,
   and bt_sample_of_kpos inverts it;
-- bt_swz maps (row < 128, K byte < 128) one to one onto the 16 KB tile, keeps
-  each row inside its own 128-byte line and each 16-byte chunk contiguous, and
-  permutes the chunks of row r by XOR with r mod 8 (the 128-byte swizzle).
+- bt_swz maps (row < 128, K byte < 128) one to one onto the 16 KB tile;
+- bt_swz equals the 128-byte swizzle as the public descriptions state it,
+  written here independently of bt_swz: take the unswizzled byte address
+  a = 128 r + kk of a tile of 128-byte rows and XOR its bits 7-9 into its bits
+  4-6 (CuTe's Swizzle<3, 4, 3>: a ^ ((a & 0x380) >> 3)), and a few offsets
+  worked out by hand from the rule "16-byte chunk c of row r lands at chunk
+  c XOR (r mod 8) of the same 128-byte row; rows r >= 8 start 1024 bytes per 8
+  rows further".
 """
 import os
 import shutil
@@ -34,10 +39,15 @@ int main() {
         for (int kk = 0; kk < 128; ++kk) {
             const int o = bt_swz(r, kk);
             if (o < 0 || o >= 16384 || hit[o]++) { ++bad; continue; }
-            if (o / 128 != (r >> 3) * 8 + (r & 7)) ++bad;                 // row r's own 128-byte line
-            if ((o & 15) != (kk & 15)) ++bad;                             // chunks stay contiguous
-            if (((o >> 4) & 7) != (((kk >> 4) ^ (r & 7)) & 7)) ++bad;     // chunk c of row r at c ^ (r mod 8)
+            const int a = 128 * r + kk;                                   // unswizzled address
+            if (o != (a ^ ((a & 0x380) >> 3))) ++bad;                      // Swizzle<3, 4, 3>
         }
+    // (row, K byte) -> offset, by hand
+    const int hand[][3] = {{0, 0, 0},       {0, 17, 17},    {1, 0, 144},    {1, 16, 128},  {1, 31, 143},
+                           {2, 32, 128 * 2 + 0}, {3, 48, 384}, {7, 127, 911}, {8, 0, 1024}, {9, 40, 1208},
+                           {15, 112, 1920 + 0}, {127, 5, 16373}};
+    for (const auto& e : hand)
+        if (bt_swz(e[0], e[1]) != e[2]) { printf("hand %d %d -> %d\n", e[0], e[1], bt_swz(e[0], e[1])); ++bad; }
     printf("%d\n", bad);
     return 0;
 }
