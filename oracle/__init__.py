@@ -35,7 +35,7 @@ def build(force: bool = False) -> str:
     src = os.path.join(_HERE, "oracle.c")
     if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
         tmp = out + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+        subprocess.check_call(["gcc", "-O3", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
                                "-shared", "-o", tmp, src, "-lm"])
         os.replace(tmp, out)
     return out
@@ -71,6 +71,8 @@ def _lib():
             lib.orc_rmatvec.argtypes = [P(_Mat), vp, vp]
             lib.orc_matvec_rows.argtypes = [P(_Mat), vp, vp, i64, vp]
             lib.orc_rmatvec_cols.argtypes = [P(_Mat), vp, vp, i64, vp]
+            lib.orc_matmat.argtypes = [P(_Mat), vp, i64, vp]
+            lib.orc_rmatmat.argtypes = [P(_Mat), vp, i64, vp]
             lib.orc_jacobi_svd.argtypes = [i64, i64, vp, vp, vp, vp]
             lib.orc_jacobi_svd.restype = ctypes.c_int
             lib.orc_gkl.argtypes = [P(_Mat), P(_Opts), vp, vp, vp, vp, vp, P(_Info), vp, vp, vp]
@@ -137,6 +139,22 @@ class Matrix:
         x = np.empty(self.m)
         _lib().orc_rmatvec(ctypes.byref(self._c()), u.ctypes.data, x.ctypes.data)
         return x
+
+    def matmat(self, X):
+        """A X for an m x k matrix X (each column as matvec computes it)."""
+        X = np.asfortranarray(X, dtype=np.float64)
+        k = X.shape[1]
+        Y = np.empty((self.n, k), order="F")
+        _lib().orc_matmat(ctypes.byref(self._c()), X.ctypes.data, k, Y.ctypes.data)
+        return Y
+
+    def rmatmat(self, U):
+        """A^T U for an n x k matrix U (each column as rmatvec computes it)."""
+        U = np.asfortranarray(U, dtype=np.float64)
+        k = U.shape[1]
+        X = np.empty((self.m, k), order="F")
+        _lib().orc_rmatmat(ctypes.byref(self._c()), U.ctypes.data, k, X.ctypes.data)
+        return X
 
     def matvec_rows(self, v, rows):
         v, rows = _f64(v), np.ascontiguousarray(rows, dtype=np.int64)

@@ -145,6 +145,55 @@ void orc_rmatvec_cols(const orc_mat *M, const double *u, const int64_t *cols, in
     }
 }
 
+/* Y = A X for k vectors at once (X m x k, Y n x k, column-major): the
+ * definition y_ic = sum_j A_ij x_jc, j ascending, each product and sum
+ * rounded as written -- every column equals orc_matvec of that column.  Work
+ * is split over tiles of 512 samples (each task walks all SNPs for its tile,
+ * so its rows of Y stay in cache); the entries of a SNP row are formed once
+ * per tile and used for all k columns. */
+void orc_matmat(const orc_mat *M, const double *X, int64_t k, double *Y) {
+    const int64_t n = M->n, m = M->m, T = 512;
+    const int64_t tiles = (n + T - 1) / T;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t t = 0; t < tiles; ++t) {
+        const int64_t i0 = t * T, i1 = i0 + T < n ? i0 + T : n, len = i1 - i0;
+        double a[512];
+        for (int64_t c = 0; c < k; ++c)
+            for (int64_t i = i0; i < i1; ++i) Y[i + c * n] = 0.0;
+        for (int64_t j = 0; j < m; ++j) {
+            for (int64_t i = 0; i < len; ++i) a[i] = entry(M, i0 + i, j);
+            for (int64_t c = 0; c < k; ++c) {
+                const double xj = X[j + c * m];
+                double *y = Y + i0 + c * n;
+                for (int64_t i = 0; i < len; ++i) y[i] += a[i] * xj;
+            }
+        }
+    }
+}
+
+/* X = A^T U for k vectors at once (U n x k, X m x k, column-major): x_jc =
+ * sum_i A_ij u_ic, i ascending -- every column equals orc_rmatvec of that
+ * column.  One SNP row per task; its entries are formed once for all k. */
+void orc_rmatmat(const orc_mat *M, const double *U, int64_t k, double *X) {
+    const int64_t n = M->n, m = M->m;
+#pragma omp parallel
+    {
+        double *a = (double *)malloc(sizeof(double) * (size_t)n);
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t j = 0; j < m; ++j) {
+            if (!a) continue;
+            for (int64_t i = 0; i < n; ++i) a[i] = entry(M, i, j);
+            for (int64_t c = 0; c < k; ++c) {
+                const double *u = U + c * n;
+                double acc = 0.0;
+                for (int64_t i = 0; i < n; ++i) acc += a[i] * u[i];
+                X[j + c * m] = acc;
+            }
+        }
+        free(a);
+    }
+}
+
 /* ------------------------------------------------------------ Jacobi SVD */
 
 /* One-sided Jacobi SVD (Hestenes 1958; Demmel & Veselic 1992) of the r x c

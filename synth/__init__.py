@@ -38,6 +38,37 @@ def build(force: bool = False) -> str:
     return out
 
 
+_LIB_GPU = None
+
+
+def build_gpu(force: bool = False) -> str:
+    """Compile synth_gpu.cu (the device twin of synth_pack) with nvcc for
+    sm_103a, FP contraction off, into a shared library; return its path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    out = os.path.join(_BUILD, "libsynth_gpu.so")
+    src = os.path.join(_HERE, "synth_gpu.cu")
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
+        tmp = out + f".{os.getpid()}.tmp"
+        nvcc = os.environ.get("NVCC", "nvcc")
+        subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-fmad=false",
+                               "-Xcompiler", "-fPIC", "-shared", "-o", tmp, src])
+        os.replace(tmp, out)
+    return out
+
+
+def _lib_gpu():
+    global _LIB_GPU
+    with _LOCK:
+        if _LIB_GPU is None:
+            lib = ctypes.CDLL(build_gpu())
+            vp, i64 = ctypes.c_void_p, ctypes.c_int64
+            lib.synth_pack_gpu.argtypes = [i64, i64, i64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64,
+                                           vp, vp, vp, vp, vp, vp]
+            lib.synth_pack_gpu.restype = ctypes.c_int
+            _LIB_GPU = lib
+    return _LIB_GPU
+
+
 class _Params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("stride", ctypes.c_int64),
                 ("n_pops", ctypes.c_int32), ("admixture", ctypes.c_int32),
@@ -180,6 +211,39 @@ def paper_model(spec: ModelSpec, out: np.ndarray | None = None) -> Genotypes:
     if rc != 0:
         raise ValueError("bad model spec")
     return Genotypes(spec, out, np.zeros((0, spec.m)), np.zeros((spec.n, 0)))
+
+
+def genotypes_device(spec: GenoSpec, device="cuda"):
+    """The packed matrix of ``genotypes(spec)``, byte for byte, drawn on a CUDA
+    device (synth_gpu.cu): the per-SNP and per-sample parameters f and q come
+    from the same C code on the host, the per-entry draws from the device.
+    Returns (packed uint8 tensor [m, stride] on the device, f, q)."""
+    import math
+
+    import torch
+    lib = _lib()
+    p = spec._params()
+    f = np.empty((spec.n_pops, spec.m), dtype=np.float64)
+    q = np.empty((spec.n, spec.n_pops), dtype=np.float64)
+    if lib.synth_population(ctypes.byref(p), f.ctypes.data, q.ctypes.data) != 0:
+        raise ValueError("bad genotype spec")
+    dev = torch.device(device)
+    q64 = torch.from_numpy(q).to(dev)
+    f64 = torch.from_numpy(f).to(dev)
+    q32 = torch.from_numpy(q.astype(np.float32)).to(dev)
+    f32 = torch.from_numpy(f.astype(np.float32)).to(dev)
+    out = torch.empty((spec.m, spec.stride), dtype=torch.uint8, device=dev)
+    # (double) r < miss_rate * 2^32  <=>  r < ceil(miss_rate * 2^32) for an integer r
+    miss_int = min(int(math.ceil(spec.miss_rate * 4294967296.0)), 1 << 32)
+    with torch.cuda.device(dev):
+        stream = torch.cuda.current_stream().cuda_stream
+        rc = _lib_gpu().synth_pack_gpu(spec.n, spec.m, spec.stride, spec.n_pops, spec.seed, miss_int,
+                                       q64.data_ptr(), f64.data_ptr(), q32.data_ptr(), f32.data_ptr(),
+                                       out.data_ptr(), stream)
+        if rc != 0:
+            raise RuntimeError(f"synth_pack_gpu failed ({rc})")
+        torch.cuda.current_stream().synchronize()
+    return out, f, q
 
 
 def normal_vec(seed: int, stream: int, length: int) -> np.ndarray:

@@ -102,6 +102,26 @@ def test_products_match_dense(weights):
     assert np.allclose(M.rmatvec_cols(u, cols), (A.T @ u)[cols], rtol=1e-12)
 
 
+@pytest.mark.parametrize("n,m,k", [(157, 211, 3), (1030, 97, 5), (1, 3, 1)])
+def test_block_products_match_dense(n, m, k):
+    """A X and A^T U for k vectors against NumPy's dense products (a library
+    routine), across more than one 512-sample tile and a ragged tail; and each
+    column equal, bit for bit, to the single-vector product (same sums in the
+    same order)."""
+    g, M = _random_case(n, m, 21 + k)
+    M = oracle.Matrix(g.packed, n, M.mu, M.d, s=synth.uniform_vec(7, 0, n, 0.5, 1.5),
+                      w=synth.uniform_vec(7, 1, m, 0.5, 1.5))
+    A = M.dense()
+    X = np.stack([synth.normal_vec(9, c, m) for c in range(k)], axis=1)
+    U = np.stack([synth.normal_vec(10, c, n) for c in range(k)], axis=1)
+    Y, Z = M.matmat(X), M.rmatmat(U)
+    assert np.allclose(Y, A @ X, rtol=1e-12, atol=1e-12)
+    assert np.allclose(Z, A.T @ U, rtol=1e-12, atol=1e-12)
+    for c in range(k):
+        assert np.array_equal(Y[:, c], M.matvec(X[:, c]))
+        assert np.array_equal(Z[:, c], M.rmatvec(U[:, c]))
+
+
 def test_unit_vector_products_are_single_rounded_entries():
     # A e_j is column j exactly: ((double)c - mu_j) * d_j with no other rounding
     n, m = 90, 40
