@@ -210,8 +210,10 @@ int gkl_matmat(gkl_handle* h, int32_t transpose, int32_t q, int32_t digits, cons
  * the SNP chunk count of the product (4 to 8 blocks per SM over the sample
  * tiles of 128 to 256 words: 196 in FP64 and 228 in FP32 for n = 10,000 on
  * 152 SMs);
- * sizes beyond 32 MiB are rejected with GKL_ERR_ARG and a message that gives
- * both numbers.  The first call on a device looks up the array's device
+ * sizes beyond 32 MiB less 256 bytes (the last 256 hold the error word of the
+ * FP32 product's bounded TMA waits, which this call cannot report: it does
+ * not synchronise) are rejected with GKL_ERR_ARG and a message that gives both
+ * numbers.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress); make that first call before any stream
  * capture.  All calls share the array and it keeps the last call's contents
  * (each call writes every element it reads, so nothing needs clearing); calls

@@ -608,8 +608,8 @@ int gkl_init(gkl_handle** out, const uint8_t* packed, int64_t n, int64_t m, int6
         gkl_destroy(h);
         return GKL_ERR_CUDA;
     }
-    // the FP32 A^T u runs on the tensor cores: TMA descriptor, kernel attributes
-    if (!tc_prepare(h)) {
+    // the FP32 products read the packed matrix through TMA descriptors; A^T u runs on the tensor cores
+    if (!make_mv_map(packed, stride, m, h->mv_map) || !tc_prepare(h)) {
         cudaGetLastError();
         set_err(nullptr, GKL_ERR_CUDA, "gkl_init: the tensor-core A^T u could not be prepared");
         gkl_destroy(h);

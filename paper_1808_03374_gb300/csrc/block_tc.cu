@@ -225,7 +225,7 @@ __device__ __forceinline__ void bt_rmv_epilogue(const BtRmvArgs& a, uint32_t tme
             s_dw[et] = j < a.m ? a.d[j] * (a.w ? (double)a.w[j] : 1.0) : 0.0;
         }
         asm volatile("bar.sync 1, 128;\n" ::: "memory");
-        if (ok && !bar_wait(afull0 + 8u * acc, (li >> 1) & 1u)) {
+        if (ok && !tc::bar_wait_warp(afull0 + 8u * acc, (li >> 1) & 1u)) {
             atomicCAS(a.err, 0, 20);
             ok = false;
         }
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(kThreadsBT, 1) k_bt_rmv(const __grid_constant_
         for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
             for (int k = 0; k < a.nstages && ok; ++k, ++ps) {
                 const int sp = (int)(ps % kRP);
-                if (!bar_wait(pfull(sp), (ps / kRP) & 1u)) {
+                if (!tc::bar_wait_warp(pfull(sp), (ps / kRP) & 1u)) {
                     fail(18);
                     ok = false;
                     break;
@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(kThreadsBT, 1) k_bt_rmv(const __grid_constant_
                     const int sd = (int)(it % kRD);
                     const uint4 P = *reinterpret_cast<const uint4*>(gP + sp * kBoxBytes + row * 128 +
                                                                      ((((2 * qq + hh) ^ (row & 7))) << 4));
-                    if (!bar_wait(dempty(sd), ((it / kRD) & 1u) ^ 1u)) {
+                    if (!tc::bar_wait_warp(dempty(sd), ((it / kRD) & 1u) ^ 1u)) {
                         fail(19);
                         ok = false;
                         break;
@@ -454,7 +454,7 @@ __device__ __forceinline__ void bt_mv_epilogue(const BtMvArgs& a, uint32_t tmem,
     uint32_t li = 0;
     for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++li) {
         const int blk = item % a.nblocks, ch = item / a.nblocks;
-        if (!bar_wait(afull, li & 1u)) {
+        if (!tc::bar_wait_warp(afull, li & 1u)) {
             atomicCAS(a.err, 0, 30);
             break;
         }
@@ -621,7 +621,7 @@ __global__ void __launch_bounds__(kThreadsBT, 1) k_bt_mv(const __grid_constant__
             stages_of(item, s0, ns);
             for (int k = 0; k < ns && ok; ++k, ++ps) {
                 const int sp = (int)(ps % kVP);
-                if (!bar_wait(pfull(sp), (ps / kVP) & 1u)) {
+                if (!tc::bar_wait_warp(pfull(sp), (ps / kVP) & 1u)) {
                     fail(28);
                     ok = false;
                     break;
@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(kThreadsBT, 1) k_bt_mv(const __grid_constant__
                     const int row = 32 * ks + lane, g = lane >> 3, rr = lane & 7;
                     const uint4 P = *reinterpret_cast<const uint4*>(gP + sp * kBoxBytes + row * 128 +
                                                                      (((dw ^ (row & 7))) << 4));
-                    if (!bar_wait(dempty(sd), ((it / kVD) & 1u) ^ 1u)) {
+                    if (!tc::bar_wait_warp(dempty(sd), ((it / kVD) & 1u) ^ 1u)) {
                         fail(29);
                         ok = false;
                         break;

@@ -9,6 +9,21 @@
 
 #define GKL_MAX_ELL 128
 
+// Diagnostic builds (-DGKL_DEBUG_SYNC_CHECKS) synchronise after each kernel of
+// the product launchers and print the first one whose execution failed.
+#ifdef GKL_DEBUG_SYNC_CHECKS
+#include <cstdio>
+#define GKL_DEBUG_SYNC(st, what)                                                              \
+    do {                                                                                      \
+        cudaError_t dbg_e = cudaStreamSynchronize(st);                                        \
+        if (dbg_e != cudaSuccess) fprintf(stderr, "GKL_DEBUG %s: %s\n", what, cudaGetErrorString(dbg_e)); \
+    } while (0)
+#else
+#define GKL_DEBUG_SYNC(st, what) \
+    do {                         \
+    } while (0)
+#endif
+
 namespace gkl {
 
 // Scalars of one Lanczos run, resident in device memory so that the step
@@ -103,9 +118,11 @@ struct gkl_handle {
     size_t gws_bytes;
     // tensor-core (tcgen05) A^T u: 0 = not prepared, 1 = ready, -1 = unavailable
     int tc_state;
-    alignas(64) unsigned char tc_map[128];  // TMA descriptor of the packed matrix
-    int64_t* miss_off;   // CSR of the missing codes per SNP (m + 1 offsets), built by tc_prepare
-    uint32_t* miss_idx;  // sample indices, ascending per SNP
+    alignas(64) unsigned char tc_map[128];  // TMA descriptor of the packed matrix (A^T u: 128 B x 128 rows, swizzled)
+    alignas(64) unsigned char mv_map[128];  // TMA descriptor for A v (256 B x 32 rows, no swizzle)
+    int* mv_err;     // error word of the A v kernel when the handle has no aux buffer (allocation-free product)
+    int64_t* miss_off;   // list of the missing codes per SNP (m + 1 offsets), built by tc_prepare
+    uint32_t* miss_idx;  // their sample indices, ascending per SNP
     int64_t miss_nnz;
     char err[512];
 };
@@ -163,12 +180,14 @@ enum MemKind { MEM_BAD = 0, MEM_DEVICE = 1, MEM_HOST = 2 };
 int mem_kind(const void* p, int device);
 // S = U diag(sigma) (n x k, column-major) in the type of prec (GKL_FP64: double, else float)
 cudaError_t launch_scores(cudaStream_t st, int prec, const void* U, const double* sigma, int64_t n, int k, void* S);
-// tcgen05 A^T u (FP32 path, packed_tc.cu); tc_prepare builds the missing-code list once per handle.
+// tcgen05 A^T u (FP32 path, packed_tc.cu); tc_prepare builds the TMA descriptor and the
+// list of missing codes once per handle.
 bool tc_prepare(gkl_handle* h);
 size_t rmv_tc_scratch_bytes(const gkl_handle* h);
 cudaError_t launch_rmatvec_tc(const gkl_handle* h, const float* u, float* x, void* scratch, const Sv* sv,
                               const FinArgs* fa, cudaEvent_t ev0, cudaEvent_t ev1, int* nlaunch);
 
+bool make_mv_map(const uint8_t* packed, int64_t stride, int64_t m, void* out);
 cudaError_t launch_colstats(const uint8_t* packed, int64_t n, int64_t m, int64_t stride, double* mu, double* scale,
                             int64_t* nobs, cudaStream_t st);
 

@@ -15,6 +15,12 @@
 // scratch element it later reads, so nothing needs clearing between calls.
 // Calls that overlap on the GPU (concurrent streams or host threads) race on
 // the array and must be serialised by the caller.
+//
+// The FP32 product streams the matrix through TMA copies whose waits are
+// bounded (about two seconds); the last 256 bytes of the array hold the word a
+// wait that runs out would set.  The call does not synchronise, so such an
+// event (a GPU stalled for seconds) is not reported to it: y is then
+// undefined.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -83,14 +89,21 @@ extern "C" int gkl_matvec_noalloc(const uint8_t* packed, int64_t n, int64_t m, i
     const gkl::MvPlan p = gkl::plan_products(&h);
     const size_t elem = prec == GKL_FP64 ? sizeof(double) : sizeof(float);
     const size_t need = ((size_t)p.mv_chunks(prec == GKL_FP32) * (size_t)p.ldp + (size_t)m * 4) * elem;
-    if (need > kStaticScratchBytes)
+    if (need > kStaticScratchBytes - 256)
         return set_err(nullptr, GKL_ERR_ARG,
                        "gkl_matvec_noalloc: n=%lld, m=%lld needs %zu bytes of scratch, above its static maximum of "
                        "%zu bytes; use gkl_matvec",
-                       (long long)n, (long long)m, need, kStaticScratchBytes);
+                       (long long)n, (long long)m, need, kStaticScratchBytes - 256);
     void* scratch = nullptr;
     int st = scratch_address(h.device, &scratch);
     if (st) return st;
+    if (prec == GKL_FP32) {
+        if (!gkl::make_mv_map(packed, stride, m, h.mv_map))
+            return set_err(nullptr, GKL_ERR_CUDA, "gkl_matvec_noalloc: TMA descriptor of the packed matrix");
+        h.mv_err = reinterpret_cast<int*>(static_cast<unsigned char*>(scratch) + kStaticScratchBytes - 256);
+        e = cudaMemsetAsync(h.mv_err, 0, sizeof(int), h.stream);
+        if (e != cudaSuccess) return gkl::cuda_err(nullptr, e, "gkl_matvec_noalloc error word");
+    }
     e = prec == GKL_FP64
             ? gkl::launch_matvec<double>(&h, (const double*)v, (double*)y, scratch, nullptr, nullptr)
             : gkl::launch_matvec<float>(&h, (const float*)v, (float*)y, scratch, nullptr, nullptr);

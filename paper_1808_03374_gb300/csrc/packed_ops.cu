@@ -12,14 +12,19 @@
 #include <algorithm>
 #include <mutex>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "epilogue.cuh"
 #include "gkl_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace gkl {
 
 namespace {
 constexpr int kThreads = 256;   // threads per block of the product kernels
 constexpr int kRowBatch = 32;   // SNP rows staged per batch
+constexpr int kMvBoxBytesHost = 256, kMvRowsHost = 32;  // TMA box of the FP32 A v kernel
 }
 
 // ------------------------------------------------------------------ stats
@@ -72,6 +77,32 @@ cudaError_t launch_colstats(const uint8_t* packed, int64_t n, int64_t m, int64_t
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ TMA view for A v
+
+// TMA descriptor of the packed matrix for the FP32 A v kernel: a 2-D uint8
+// tensor (stride x m) read in boxes of 256 bytes x 32 rows, no swizzle.
+// Host-only (no device memory is allocated); false if the driver entry point
+// is unavailable or the descriptor is rejected.
+bool make_mv_map(const uint8_t* packed, int64_t stride, int64_t m, void* out) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || fn == nullptr) {
+        cudaGetLastError();
+        return false;
+    }
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    const cuuint64_t gdim[2] = {(cuuint64_t)stride, (cuuint64_t)m};
+    const cuuint64_t gstride[1] = {(cuuint64_t)stride};
+    const cuuint32_t box[2] = {(cuuint32_t)kMvBoxBytesHost, (cuuint32_t)kMvRowsHost};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(reinterpret_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                        const_cast<uint8_t*>(packed), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 // ------------------------------------------------------------------ plan
 
 MvPlan plan_products(const gkl_handle* h) {
@@ -86,24 +117,24 @@ MvPlan plan_products(const gkl_handle* h) {
     p.rows_per_chunk = (int)rpc;
     p.chunks = (int)((h->m + rpc - 1) / rpc);
     p.ldp = p.nwords * 16;
-    // FP32 A.v: the block width (a multiple of 32 words) and chunking that give
-    // the busiest SM the fewest word-rows, one wave at the kernel's residency of
-    // 64 registers a thread; every block covers at least one 256-row batch.
+    // FP32 A.v (TMA-fed pair-table kernel, one CTA of 256 words per SM): the SNP
+    // chunking that gives the busiest SM the fewest rows, every chunk at least
+    // one 256-row table batch (rows a multiple of the 32-row stage)
     {
+        const int sms = std::max(1, h->num_sms);
+        const int64_t tiles = (p.nwords + 255) / 256;
         double best = 0.0;
-        for (int nt = 256; nt >= 128; nt -= 32) {
-            const int per_sm = 65536 / (64 * nt);
-            const int64_t tiles = (p.nwords + nt - 1) / nt;
-            int64_t chunks = std::max<int64_t>(1, (int64_t)per_sm * std::max(1, h->num_sms) / tiles);
+        for (int waves = 1; waves <= 12; ++waves) {
+            int64_t chunks = std::max<int64_t>(1, (waves * (int64_t)sms + tiles - 1) / tiles);
             int64_t rpc = (h->m + chunks - 1) / chunks;
             rpc = std::max<int64_t>(rpc, 256);
-            rpc = (rpc + 7) / 8 * 8;
+            rpc = (rpc + 31) / 32 * 32;
             chunks = (h->m + rpc - 1) / rpc;
-            const int64_t blocks_sm = (tiles * chunks + std::max(1, h->num_sms) - 1) / std::max(1, h->num_sms);
-            const double load = (double)blocks_sm * (double)rpc * (double)nt;
+            const int64_t blocks_sm = (tiles * chunks + sms - 1) / sms;
+            const double load = (double)blocks_sm * (double)rpc;
             if (best == 0.0 || load < 0.99 * best) {
                 best = load;
-                p.pair_threads = nt;
+                p.pair_threads = 256;
                 p.pair_tiles = (int)tiles;
                 p.pair_chunks = (int)chunks;
                 p.pair_rpc = (int)rpc;
@@ -227,79 +258,139 @@ __device__ __forceinline__ void pair_lookups(uint32_t wa, uint32_t wb, uint32_t 
     }
 }
 
-__global__ void __launch_bounds__(kPairMaxThreads, 4)
-    k_mv_pair(const uint8_t* __restrict__ packed, int64_t stride, int64_t nwords, int64_t m, int rpc,
-              const float* __restrict__ lut, float* __restrict__ part, int64_t ldp) {
-    // two table buffers, each starting on a 256-byte boundary of the shared window
-    __shared__ __align__(16) float tabs[2 * kPairTab + 64];
-    const uint32_t tabs_sh = (uint32_t)__cvta_generic_to_shared(tabs);
-    const uint32_t tb0 = (tabs_sh + 255u) & ~255u;
-    const int nt = blockDim.x;
-    const int64_t word = (int64_t)blockIdx.x * nt + threadIdx.x;
+// The FP32 A v kernel: one CTA per (sample tile of 256 words = 4,096 samples,
+// SNP chunk), 8 consumer warps (one 16-sample word per thread) and one copy
+// warp.  The copy warp's lane 0 streams the tile's rows through a ring of
+// shared-memory stages with TMA (32 rows x four 256-byte boxes per stage, no
+// swizzle: a warp's 32 words of a row are 128 contiguous bytes, one wavefront),
+// so the consumers only wait on full stages and spend their issue slots on
+// table lookups.  Pair tables are built per 256-row batch by consumer threads
+// (double-buffered; the consumers meet at a named barrier once per batch).
+constexpr int kMvWords = 256;                  // words (16 samples each) per tile
+constexpr int kMvConsumers = kMvWords;         // consumer threads
+constexpr int kMvThreads = kMvConsumers + 32;  // + one copy warp
+constexpr int kMvRows = 32;                    // rows per stage
+constexpr int kMvBoxBytes = 256;               // box width (bytes of one row)
+constexpr int kMvBoxes = kMvWords * 4 / kMvBoxBytes;
+constexpr int kMvStageBytes = kMvRows * kMvWords * 4;  // 32 KB
+constexpr int kMvStages = 4;
+constexpr int kMvTabOff = kMvStages * kMvStageBytes;      // two table buffers of 8 KB
+constexpr int kMvBarOff = kMvTabOff + 2 * kPairTab * 4;
+constexpr int kMvSmem = 1024 + kMvBarOff + 256;
+static_assert(kPairRows % kMvRows == 0, "a table batch covers whole stages");
+
+__global__ void __launch_bounds__(kMvThreads, 1)
+    k_mv_pair(const __grid_constant__ CUtensorMap tmap, int64_t nwords, int64_t m, int rpc,
+              const float* __restrict__ lut, float* __restrict__ part, int64_t ldp, int* err) {
+    extern __shared__ uint8_t mv_smem_raw[];
+    const uint32_t raw = tc::sm_addr(mv_smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* sb = mv_smem_raw + (base - raw);
+    const uint32_t sBar = base + kMvBarOff;
+    auto full = [&](int s) { return sBar + 8u * s; };
+    auto empty = [&](int s) { return sBar + 8u * (kMvStages + s); };
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t j0 = (int64_t)blockIdx.y * rpc;
     const int64_t j1 = min(m, j0 + (int64_t)rpc);
-    const bool active = word < nwords;
-    const int64_t wstride = stride >> 2;
-    const uint32_t* base = reinterpret_cast<const uint32_t*>(packed) + (active ? word : 0);
+    const int nstage = (int)((j1 - j0 + kMvRows - 1) / kMvRows);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kMvStages; ++s) {
+            tc::bar_init(full(s), 1);
+            tc::bar_init(empty(s), kMvConsumers / 32);
+        }
+        tc::bar_init_fence();
+    }
+    __syncthreads();
+    auto fail = [&](int code) {
+        if (err) atomicCAS(err, 0, code);
+    };
 
+    if (warp == kMvConsumers / 32) {
+        // ---- copies: rows j0 .. of this tile, four 256-byte boxes per 32-row stage
+        if (lane == 0) {
+            const int x0 = (int)blockIdx.x * kMvWords * 4;
+            int s_it = 0;
+            for (; s_it < nstage; ++s_it) {
+                const int s = s_it % kMvStages;
+                if (!tc::bar_wait(empty(s), ((s_it / kMvStages) & 1) ^ 1)) {
+                    fail(41);
+                    break;
+                }
+                tc::bar_expect_tx(full(s), kMvStageBytes);
+                const int y = (int)(j0 + (int64_t)s_it * kMvRows);
+#pragma unroll
+                for (int bx = 0; bx < kMvBoxes; ++bx)
+                    tc::tma_2d(base + s * kMvStageBytes + bx * kMvRows * kMvBoxBytes, &tmap, x0 + bx * kMvBoxBytes,
+                               y, full(s));
+            }
+            // drain: every issued copy has landed before the CTA may exit
+            for (int q = s_it > kMvStages ? s_it - kMvStages : 0; q < s_it; ++q)
+                if (!tc::bar_wait(full(q % kMvStages), (q / kMvStages) & 1)) fail(42);
+        }
+        return;
+    }
+
+    // ---- consumers
+    const uint32_t tb0 = base + kMvTabOff;
+    float* tabs = reinterpret_cast<float*>(sb + kMvTabOff);
+    const int t = threadIdx.x;
+    const int64_t word = (int64_t)blockIdx.x * kMvWords + t;
+    const bool active = word < nwords;
     // the table of pair p of the batch at row jb (rows jb + 2p, jb + 2p + 1) is
     // built by thread p from the two rows' 4-entry tables: one L2 round trip
-    auto build = [&](int64_t jb, uint32_t tb) {
-        const int p = threadIdx.x;
+    auto build = [&](int64_t jb, int buf) {
+        const int p = t;
         if (p >= kPairBatch) return;
         const int64_t ra = jb + 2 * p, rb = ra + 1;
         const float4 la = ra < j1 ? __ldg(reinterpret_cast<const float4*>(lut) + ra) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 lb = rb < j1 ? __ldg(reinterpret_cast<const float4*>(lut) + rb) : make_float4(0.f, 0.f, 0.f, 0.f);
-        float4* dst = reinterpret_cast<float4*>(reinterpret_cast<char*>(tabs) + (tb - tabs_sh) + 64u * (uint32_t)p);
+        float4* dst = reinterpret_cast<float4*>(tabs + buf * kPairTab + 16 * p);
         dst[0] = make_float4(la.x + lb.x, la.y + lb.x, la.z + lb.x, la.w + lb.x);  // c_b = 0
         dst[1] = make_float4(la.x + lb.y, la.y + lb.y, la.z + lb.y, la.w + lb.y);  // c_b = 1
         dst[2] = make_float4(la.x + lb.z, la.y + lb.z, la.z + lb.z, la.w + lb.z);  // c_b = 2
         dst[3] = make_float4(la.x + lb.w, la.y + lb.w, la.z + lb.w, la.w + lb.w);  // c_b = 3
     };
-    // code words of rows r0 .. r0+7; rows past the chunk read its last row (their tables are zero)
-    auto load_group = [&](int64_t r0, uint32_t (&w)[8]) {
-        if (r0 + 8 <= j1) {
-            const uint32_t* rp = base + r0 * wstride;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) w[k] = __ldg(rp + k * wstride);
-        } else {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) w[k] = __ldg(base + min(r0 + k, j1 - 1) * wstride);
-        }
-    };
-
+    // word t of row r of a stage: box t / 64, 4 (t mod 64) bytes into the row
+    const uint32_t* wbase =
+        reinterpret_cast<const uint32_t*>(sb + (t >> 6) * kMvRows * kMvBoxBytes + 4 * (t & 63));
     float2 acc[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc[k] = make_float2(0.f, 0.f);
     const int nbatch = (int)((j1 - j0 + kPairRows - 1) / kPairRows);
-    build(j0, tb0);
-    __syncthreads();
-    uint32_t w[8];
-    if (active) load_group(j0, w);
+    build(j0, 0);
+    asm volatile("bar.sync 1, %0;\n" ::"n"(kMvConsumers) : "memory");
+    bool ok = true;
+    int s_it = 0;
     for (int i = 0; i < nbatch; ++i) {
         const int64_t jb = j0 + (int64_t)i * kPairRows;
         const uint32_t tb = tb0 + (uint32_t)(i & 1) * (kPairTab * 4);
-        if (i + 1 < nbatch) build(jb + kPairRows, tb0 + (uint32_t)((i + 1) & 1) * (kPairTab * 4));
-        if (active) {
-            const int ng = (int)min((int64_t)(kPairRows / 8), (j1 - jb + 7) / 8);
-            for (int g = 0; g < ng; ++g) {
-                uint32_t nw[8];
-                const bool more = g + 1 < ng || i + 1 < nbatch;
-                if (more) load_group(g + 1 < ng ? jb + 8 * (g + 1) : jb + kPairRows, nw);
-                const uint32_t gb = tb + 256u * (uint32_t)g;
+        if (i + 1 < nbatch) build(jb + kPairRows, (i + 1) & 1);
+        const int ns = min(kPairRows / kMvRows, nstage - i * (kPairRows / kMvRows));
+        for (int q = 0; q < ns && ok; ++q, ++s_it) {
+            const int s = s_it % kMvStages;
+            if (!tc::bar_wait_warp(full(s), (s_it / kMvStages) & 1)) {
+                fail(43);
+                ok = false;
+                break;
+            }
+            const uint32_t* wr = wbase + s * (kMvStageBytes / 4);
+#pragma unroll
+            for (int g = 0; g < kMvRows / 8; ++g) {
+                uint32_t w[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) w[k] = wr[(8 * g + k) * (kMvBoxBytes / 4)];
+                const uint32_t gb = tb + 256u * (uint32_t)(q * (kMvRows / 8) + g);
                 pair_lookups<0>(w[0], w[1], gb, acc);
                 pair_lookups<1>(w[2], w[3], gb, acc);
                 pair_lookups<2>(w[4], w[5], gb, acc);
                 pair_lookups<3>(w[6], w[7], gb, acc);
-                if (more) {
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) w[k] = nw[k];
-                }
             }
+            __syncwarp();
+            if (lane == 0) tc::bar_arrive(empty(s));
         }
-        __syncthreads();
+        asm volatile("bar.sync 1, %0;\n" ::"n"(kMvConsumers) : "memory");
     }
-    if (!active) return;
+    if (!active || !ok) return;
     float4* out = reinterpret_cast<float4*>(part + (int64_t)blockIdx.y * ldp + word * 16);
 #pragma unroll
     for (int k = 0; k < 4; ++k) out[k] = make_float4(acc[2 * k].x, acc[2 * k].y, acc[2 * k + 1].x, acc[2 * k + 1].y);
@@ -399,22 +490,25 @@ cudaError_t launch_matvec(const gkl_handle* h, const T* v, T* y, void* scratch, 
     T* part = static_cast<T*>(scratch);
     T* lut = part + (size_t)chunks * (size_t)p.ldp;
     cudaStream_t st = h->stream;
+    GKL_DEBUG_SYNC(st, "before A.v");
     k_mv_table<T><<<(unsigned)((h->m + 255) / 256), 256, 0, st>>>(h->m, h->mu, h->d, h->w, v, lut);
+    GKL_DEBUG_SYNC(st, "k_mv_table");
     if (ev0) cudaEventRecord(ev0, st);
     if constexpr (fp32) {
-        // up to eight blocks of 16.6 KB tables on one SM
-        static std::once_flag carveout;
-        std::call_once(carveout, [] {
-            cudaFuncSetAttribute(k_mv_pair, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxShared);
-        });
-        k_mv_pair<<<dim3((unsigned)p.pair_tiles, (unsigned)p.pair_chunks), p.pair_threads, 0, st>>>(
-            h->packed, h->stride, p.nwords, h->m, p.pair_rpc, reinterpret_cast<const float*>(lut),
-            reinterpret_cast<float*>(part), p.ldp);
+        static std::once_flag attr;
+        std::call_once(attr, [] { cudaFuncSetAttribute(k_mv_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, kMvSmem); });
+        alignas(64) CUtensorMap map;
+        static_assert(sizeof(CUtensorMap) == sizeof(h->mv_map), "tensor map size");
+        memcpy(&map, h->mv_map, sizeof(map));
+        int* err = h->aux ? reinterpret_cast<int*>(reinterpret_cast<char*>(h->aux) + kAuxErrOffset) : h->mv_err;
+        k_mv_pair<<<dim3((unsigned)p.pair_tiles, (unsigned)p.pair_chunks), kMvThreads, kMvSmem, st>>>(
+            map, p.nwords, h->m, p.pair_rpc, reinterpret_cast<const float*>(lut), reinterpret_cast<float*>(part), p.ldp,
+            err);
     } else
         k_mv_part<T><<<dim3((unsigned)p.tiles, (unsigned)p.chunks), kThreads, 0, st>>>(
             h->packed, h->stride, p.nwords, h->m, p.rows_per_chunk, lut, part, p.ldp);
     if (ev1) cudaEventRecord(ev1, st);
+    GKL_DEBUG_SYNC(st, "A.v main kernel");
     if (nlaunch) *nlaunch = 3;
     FinArgs f{};
     Sv s{};
@@ -423,6 +517,7 @@ cudaError_t launch_matvec(const gkl_handle* h, const T* v, T* y, void* scratch, 
     // 32 outputs per block pass; at most 4 blocks per SM (the partial-norm buffer's size)
     const int fblocks = (int)std::min<int64_t>((h->n + 31) / 32, 4 * (int64_t)h->num_sms);
     k_mv_fin<T><<<(unsigned)std::max(1, fblocks), 256, 0, st>>>(part, p.ldp, chunks, h->n, h->s, y, f, s);
+    GKL_DEBUG_SYNC(st, "k_mv_fin");
     return cudaGetLastError();
 }
 

@@ -3,48 +3,49 @@
 // (A as defined in gkl.h; the per-step product of GKL bidiagonalisation,
 // section 3 of arXiv:1808.03374).
 //
-// The contraction over samples is exact integer arithmetic on the 5th-generation
-// tensor cores (tcgen05, kind::f8f6f4):
-//  * u~ in fixed point: u~'_i = S sum_{p<7} delta_{p,i} 16^-(p+1) = S z_i 2^-28,
-//    S = 2^e >= max|u~|, digits delta in [-16, 16] (exact in e4m3), z_i an
-//    integer, |u~ - u~'| <= 2^-29 S;
-//  * operand A (128 SNP rows x samples) is built in registers from the packed
-//    codes and written to tensor memory.  Code t (bits 2t, 2t+1) of a byte is
-//    read in place as e4m3: for t = 0, 2 (after one shift by 4 for t = 2) the
-//    code sits in mantissa bits 0-1, H_a(c) = 1 + c/8 (bits 0x38 | c); for
-//    t = 1, 3 it sits in bits 2-3 (mantissa MSB and exponent LSB), H_b(c) = 0.5,
-//    0.75, 1.0, 1.5 for c = 0..3 -- affine, 0.5 + c/4, on the observed codes.
-//    Five operations per 32-bit word of 16 codes;
-//  * operand B = the digit matrix (K samples x N = 16 columns, 7 used) in shared
-//    memory, 128-byte swizzled, K-major, the samples in the order the decode
-//    produces (class a: t = 0, 2 first, then class b: t = 1, 3);
-//  * eight FP32 accumulators in tensor memory (two classes x four K-step
-//    residues, so that consecutive MMAs never wait on one another), each exact:
-//    multiples of 1/8 below 2^21 for K-ranges of at most 64,000 samples;
-//  * the missing codes are sparse and fixed per matrix: their sample indices are
-//    listed once per SNP (CSR, built at the first use) and a gather kernel adds
-//    the z_i of the listed samples, as exact 64-bit integers per class, to
-//    Z_a and Z_b;
-//  * with S_a, S_b the digit sums of the two classes,
-//    sum_{obs} g u~' = S sum_p 16^-(p+1) (8 D_a[p] + 4 D_b[p]) - S sum_p 16^-(p+1) (8 S_a + 2 S_b)
-//                      - S 2^-28 (3 Z_a + 4 Z_b),
-//    sum_{missing} u~' = S 2^-28 (Z_a + Z_b).
-// Data movement: per 512-sample stage one TMA box of 128 rows x 128 bytes
-// (128-byte swizzle) brings the packed codes and one bulk copy the 8 KB digit
-// tile into a shared-memory ring.  (The copy engine walks a box row by row; a
-// 64-byte box width was measured at about 3 TB/s on this matrix.)  Warp roles
-// per CTA: one copy producer, one MMA issuer, sixteen decode warps (four per
-// TMEM sub-partition, one per 32-byte quarter of the stage) and four epilogue
-// warps.  One persistent CTA per SM walks work items (128-row tile, K-range),
-// the K-ranges of a tile consecutively so that each row is read as one
-// contiguous run (a range-major order measured 40% slower: DRAM locality).
+// The contraction over samples is exact integer arithmetic on the
+// 5th-generation tensor cores (tcgen05.mma kind::mxf4: packed e2m1 operands,
+// block scales all 1.0, FP32 accumulation in tensor memory):
+//  * u~ in fixed point: z_i = rint(u~_i 2^30 / S), S = 2^e >= max|u~|, so
+//    |z_i| <= 2^30 and u~'_i = S 2^-30 z_i is within 2^-31 S of u~_i; z_i is
+//    written with 11 balanced base-8 digits delta_p in [-4, 3] (all exact in
+//    e2m1), z_i = sum_p delta_p,i 8^(10-p);
+//  * orientation: the 11 digit rows are the MMA's A operand (M = 128 lanes of
+//    tensor memory, rows 11-127 zero), the codes of 256 SNPs its B operand
+//    (N = 256) and the samples its K axis: one MMA covers 256 SNPs x 64
+//    samples.  A 2-bit code c read as an e2m1 nibble is the value c/2, so the
+//    decode of a 32-bit word of 16 codes is two masks -- the 8 even samples
+//    (W & 0x33333333) and the 8 odd ones ((W >> 2) & 0x33333333) -- and the K
+//    order within each 16 samples is even samples, then odd ones (the digit
+//    image is written in that order);
+//  * accumulators F_p,j = sum_i (c_ij / 2) delta_p,i are multiples of 1/2
+//    below 2^23 (K-ranges of at most 2,048 stages of 512 samples), so exact in
+//    FP32, and X_j = sum_p 8^(10-p) 2 F_p,j = sum_i c_ij z_i is recombined in
+//    64-bit integers;
+//  * the missing code 3 counts as 3 there.  The missing codes are few (1-2%
+//    of the entries) and fixed per matrix: gkl_init lists them once per SNP
+//    (sample indices, ascending) and a gather kernel forms Z_j = sum of z_i
+//    over the missing samples of SNP j (exact, 64-bit), so that
+//    sum_{obs} g u~' = S 2^-30 (X_j - 3 Z_j) and
+//    sum_{obs} u~' = sum_i u~'_i - S 2^-30 Z_j.  (Summing them in the decode
+//    warps instead costs a divergent loop per code word: measured 44 warp
+//    instructions per word, four times the MMAs' time.)
+// Data movement per 512-sample stage of a 256-SNP tile: two TMA boxes of
+// 128 rows x 128 bytes (128-byte swizzle) and one bulk copy of the stage's
+// digit rows; the decode warps write the e2m1
+// operand (two 32 KB K-chunks of 256 samples, 128-byte swizzled, K-major) to
+// shared memory; one warp moves the digit rows of each K-chunk from shared to
+// tensor memory.  Warp roles: 0 copies, 1 issues the MMAs, 4 writes the
+// digits, 8 runs the epilogue (warps 4 and 8 own tensor-memory lanes 0-31),
+// 2-3, 5-7 and 9-19 decode (one SNP row and one K-chunk per thread).  One persistent CTA per SM walks work items (tile, K-range) with
+// the K-ranges of a tile consecutive, so that each row is read as one
+// contiguous run.
 //
-// Every wait is bounded (about two seconds of clock); a wait that runs out sets
-// an error word that the host reads after the solve, and the kernel drains its
-// copies and frees its tensor memory before it returns.
+// Every wait is bounded (about two seconds of clock); a wait that runs out
+// sets an error word that the host reads at its next synchronising call, and
+// the kernel drains its copies and frees its tensor memory before it returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
-#include <cuda_fp8.h>
 
 #include <algorithm>
 #include <cstring>
@@ -58,28 +59,39 @@
 namespace gkl {
 
 namespace {
-constexpr int kRows = 128;                 // SNP rows per tile = TMEM lanes = MMA M
-constexpr int kStageSamples = 512;         // samples per pipeline stage
-constexpr int kStageRowBytes = 128;        // packed bytes per row per stage
-constexpr int kStages = 8;                 // shared-memory ring depth
-constexpr int kPackedBytes = kRows * kStageRowBytes;  // 16 KB per stage
-constexpr int kDigitBytes = 16 * kStageSamples;       // 8 KB: 16 digit rows x 512 samples (4 swizzle atoms)
-constexpr int kAbuf = 2;                   // tensor-memory operand buffers (128 columns each)
-constexpr int kDigits = 7;
-constexpr int kMaxRangeStages = 125;       // 64,000 samples per K-range
-constexpr int kThreads = 704;              // 22 warps
-constexpr int kDecodeWarps = 16;
-constexpr int kDecodeWarp0 = 2, kEpiWarp0 = kDecodeWarp0 + kDecodeWarps;
+constexpr int kTile = 256;                 // SNPs per work item = MMA N
+constexpr int kStageSamples = 512;         // samples per stage: 128 packed bytes per row
+constexpr int kBox = 128;                  // rows per TMA box
+constexpr int kBoxBytes = kBox * 128;      // 16 KB
+constexpr int kStageBytes = 2 * kBoxBytes; // 32 KB of packed codes per stage
+constexpr int kUnitBytes = kTile * 128;    // decoded K-chunk: 256 rows x 128 bytes (256 samples in e2m1)
+constexpr int kRP = 3, kRD = 3, kRA = 3;   // ring depths: packed stages, decoded K-chunks, digit buffers
+constexpr int kDigitRows = 11;
+constexpr int kUnitWords = 32;             // tensor-memory columns of one K-chunk of digits (8 nibbles each)
+constexpr int kMaxRangeStages = 2048;      // |2 F_p| <= 12 x 512 x 2048 < 2^24
+constexpr int kDecodeWarps = 16;           // two groups of 8: K-chunk 0 and 1 of every stage
+constexpr int kThreads = 640;              // 20 warps
+constexpr int kWarpMma = 1, kWarpDigits = 4, kWarpEpi = 8;
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kColD = 256;            // accumulators: 2 sets x 8 x 16 columns
-constexpr int kBarOff = kStages * (kPackedBytes + kDigitBytes);
-constexpr int kSmemBytes = 1024 + kBarOff + 1024;
-// instruction descriptor: FP32 accumulate (bits 4-5 = 1), A = B = e4m3 (0), K-major
-// A and B, N = 16 (bits 17-22: N >> 3), M = 128 (bits 24-28: M >> 4)
-constexpr uint32_t kIdesc = (1u << 4) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
-}  // namespace
+constexpr uint32_t kColA = 256, kColSF = 448, kColSFA = 448, kColSFB = 480;
+constexpr int kGBytes = 2 * kDigitRows * kUnitWords * 4;  // digit rows of one stage (2 K-chunks), 2,816 bytes
+constexpr int kOffD = kRP * kStageBytes;
+constexpr int kOffG = kOffD + kRD * kUnitBytes;
+constexpr int kOffBar = kOffG + kRP * kGBytes;
+constexpr int kSmemBytes = 1024 + kOffBar + 1024;
+static_assert(kOffD % 1024 == 0, "decoded tiles must stay 1024-byte aligned");
+static_assert(kSmemBytes <= 232448, "shared memory of k_rmv_tc");
+// block-scaled instruction descriptor (kind::mxf4): A and B E2M1 (format 1,
+// bits 7-9 and 10-12), K-major, N >> 3 at bits 17-22, scale format UE8M0
+// (bit 23), M >> 4 at bits 24-28, scale-factor ids 0, K = 64 (bit 31 clear)
+constexpr uint32_t kIdesc = (1u << 7) | (1u << 10) | ((uint32_t)(kTile >> 3) << 17) | (1u << 23) | ((128u >> 4) << 24);
 
-// ---- PTX helpers (tc_ptx.cuh) ----------------------------------------------
+// decode warps: 2, 3, 5, 6, 7, 9 .. 19 -> index 0..15; index / 8 = the K-chunk of
+// every stage the warp decodes, 32 (index mod 8) + lane = its SNP row
+__device__ __forceinline__ int decode_index(int warp) {
+    return warp < 4 ? warp - 2 : (warp < 8 ? warp - 3 : warp - 4);
+}
+}  // namespace
 
 using tc::bar_arrive;
 using tc::bar_expect_tx;
@@ -90,15 +102,30 @@ using tc::desc_sw128;
 using tc::mma_commit;
 using tc::sm_addr;
 using tc::tma_2d;
-using tc::tmem_ld32;
-using tc::tmem_st16;
-__device__ __forceinline__ void mma_e4m3_ts(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t acc) {
-    tc::mma_f8_ts(d, a, bdesc, kIdesc, acc);
-}
-__device__ __forceinline__ void tc_fence_before() { tc::fence_before(); }
-__device__ __forceinline__ void tc_fence_after() { tc::fence_after(); }
 
-// ---- scale of u~ -------------------------------------------------------------
+// D (tensor memory) (+)= A (tensor memory) x B (shared memory)^T with e2m1
+// operands and block scales from tensor memory.
+__device__ __forceinline__ void mma_f4_ts(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t sfa, uint32_t sfb,
+                                          uint32_t acc) {
+    asm volatile(
+        "{.reg .pred p; setp.ne.b32 p, %5, 0; "
+        "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], [%1], %2, %6, [%3], [%4], p;}\n" ::"r"(
+            d),
+        "r"(a), "l"(bdesc), "r"(sfa), "r"(sfb), "r"(acc), "r"(kIdesc));
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
+        "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+        "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+        "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+        : "memory");
+}
+
+// ---- scale of u~ ------------------------------------------------------------
 
 // Pass 1: max|u~| and sum u~ (FP64), combined by the last block; the scale
 // S = 2^e >= max|u~| and the sum go to dsc[0..2] = {S, 1/S, sum}.
@@ -142,334 +169,333 @@ __global__ void __launch_bounds__(256) k_u_scale(const float* __restrict__ u, co
     }
 }
 
-// ---- digits of u~ -----------------------------------------------------------
+// ---- digits of u~ -------------------------------------------------------------
 
-// Position of sample `loc` (0..511) of a stage along the MMA's K axis.  Decode
-// warp q (0..3) reads bytes 32q..32q+31 of each row: code words w = 0..7 of 16
-// samples (sample 128q + 16w + 4b + t is code t of byte b).  Its operand words
-// go to tensor-memory column 16q + 2w + (t >> 1) of the class-(t & 1) region
-// (64 columns = 256 K bytes each), byte b of the column being K index
-// 4 * column + b.
-__host__ __device__ inline int tc_k_of_sample(int loc) {
-    const int q = loc >> 7, w = (loc >> 4) & 7, b = (loc >> 2) & 3, t = loc & 3;
-    return (t & 1) * 256 + 4 * (16 * q + 2 * w + (t >> 1)) + b;
+// e2m1 nibble of a balanced base-8 digit in [-4, 3] (index digit + 4):
+// -4 -3 -2 -1 0 1 2 3  ->  0xE 0xD 0xC 0xA 0x0 0x2 0x4 0x5
+__device__ __forceinline__ uint32_t e2m1_digit(int dg) {
+    constexpr uint32_t lut = 0x5420ACDEu;  // nibble k = code of digit k - 4
+    return (lut >> (4 * (dg + 4))) & 0xFu;
 }
 
-// Byte offset of (digit row p, K index kk) inside a stage's 8 KB digit tile:
-// four 128-byte-swizzled atoms of 16 rows x 128 K each.
-__host__ __device__ inline int tc_digit_offset(int p, int kk) {
-    const int atom = kk >> 7, b = kk & 127;
-    return atom * 2048 + p * 128 + ((((b >> 4) ^ (p & 7))) << 4) + (b & 15);
-}
-
-// One block per stage (512 samples): digits in e4m3 into the stage's tile, z_i
-// (int32) into z[], and the stage's digit sums per operand class (exact
-// integers) into cs[stage][16]: [class a: p = 0..6 | class b: 8 + p].
-__global__ void __launch_bounds__(512) k_u_digits_tc(const float* __restrict__ u, const float* __restrict__ s,
-                                                      int64_t n, const double* __restrict__ dsc,
-                                                      uint8_t* __restrict__ dig, int* __restrict__ cs,
-                                                      int* __restrict__ zout) {
-    const int st = blockIdx.x, loc = threadIdx.x;
-    const int64_t i = (int64_t)st * kStageSamples + loc;
-    double x = 0.0;
-    if (i < n) x = (double)u[i] * (s ? (double)s[i] : 1.0) * dsc[1];
-    uint8_t* tile = dig + (size_t)st * kDigitBytes;
-    const int kk = tc_k_of_sample(loc);
-    int sums[kDigits];
-    int z = 0;
+// One thread per tensor-memory word of a K-chunk (256 samples): the 8 samples
+// at K positions 8 w .. 8 w + 7 (K position kk of sample loc in the chunk:
+// 16 (loc / 16) + even/odd order within the 16, as the decode emits it).
+// Writes their z values and, for every digit row p < 11, the word of 8
+// nibbles: image[chunk][p][w].
+__global__ void __launch_bounds__(256) k_u_digits_f4(const float* __restrict__ u, const float* __restrict__ s,
+                                                      int64_t n, int64_t nwords, const double* __restrict__ dsc,
+                                                      uint32_t* __restrict__ image, int* __restrict__ zout) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nwords) return;
+    const int64_t chunk = t / kUnitWords;
+    const int w = (int)(t % kUnitWords);
+    const double inv = dsc[1];
+    uint32_t word[kDigitRows];
 #pragma unroll
-    for (int p = 0; p < 16; ++p) {
-        int dg = 0;
-        if (p < kDigits) {
-            x *= 16.0;
-            const double rd = rint(x);
-            x -= rd;
-            dg = (int)rd;
-            sums[p] = dg;
-            z = 16 * z + dg;
+    for (int p = 0; p < kDigitRows; ++p) word[p] = 0u;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int kk = 8 * w + e;
+        const int loc = 16 * (kk >> 4) + bt_sample_of_kpos(kk & 15);
+        const int64_t i = chunk * 256 + loc;
+        long long z = 0;
+        if (i < n) {
+            const double x = (double)u[i] * (s ? (double)s[i] : 1.0) * inv;  // |x| <= 1
+            z = __double2ll_rn(ldexp(x, 30));
         }
-        tile[tc_digit_offset(p, kk)] = (uint8_t)__nv_cvt_float_to_fp8((float)dg, __NV_SATFINITE, __NV_E4M3);
-    }
-    zout[i] = z;
-    // lanes of one warp alternate classes (t = loc & 3): reduce even and odd lanes separately
-    __shared__ int red[16][2][kDigits];
-    const int cls = loc & 1;
+        zout[i] = (int)z;
+        long long r = z;
 #pragma unroll
-    for (int p = 0; p < kDigits; ++p) {
-        int v = sums[p];
-        for (int o = 16; o > 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((loc & 31) < 2) red[loc >> 5][cls][p] = v;
+        for (int p = kDigitRows - 1; p >= 1; --p) {
+            const int dg = (int)((r + 4) & 7) - 4;
+            word[p] |= e2m1_digit(dg) << (4 * e);
+            r = (r - dg) >> 3;
+        }
+        word[0] |= e2m1_digit((int)r) << (4 * e);  // r in {-1, 0, 1}: |z| <= 2^30 = 8^10
     }
-    __syncthreads();
-    if (loc < 2 * kDigits) {
-        const int c = loc / kDigits, p = loc % kDigits;
-        int t = 0;
-        for (int w = 0; w < 16; ++w) t += red[w][c][p];
-        cs[(size_t)st * 16 + 8 * c + p] = t;
-    }
+    uint32_t* dst = image + chunk * (kDigitRows * kUnitWords) + w;
+#pragma unroll
+    for (int p = 0; p < kDigitRows; ++p) dst[p * kUnitWords] = word[p];
 }
 
 // ---- main kernel ------------------------------------------------------------
 
 struct TcArgs {
-    const uint8_t* dig;  // nstages x 8 KB digit tiles
-    const int* cs;       // nstages x 16 digit sums per class
+    const uint32_t* image;  // K-chunks x 11 x 32 digit words (k_u_digits_f4)
     int nstages, range_stages, nranges, ntiles;
     int64_t m;
-    const double* dsc;   // {S, 1/S, sum u~}
-    double* p1;          // nranges x m: S sum_p 16^-(p+1) (8 D_a + 4 D_b) over the range (range 0: - offsets)
-    double* p3;          // nranges x m: 0 (range 0: sum u~ - sum u~'); the missing terms are added later
-    int* err;            // set to a nonzero code if a wait ran out
+    const double* dsc;      // {S, 1/S, sum u~}
+    double* p1;             // nranges x m: S 2^-30 X_j over the range
+    int* err;               // set to a nonzero code if a wait ran out
 };
 
 __global__ void __launch_bounds__(kThreads, 1) k_rmv_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = sm_addr(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
-    uint8_t* sbase = smem_raw + (base - raw);
-    const uint32_t sPacked = base, sDig = base + kStages * kPackedBytes, sBar = base + kBarOff;
-    auto full = [&](int s) { return sBar + 8u * s; };
-    auto empty = [&](int s) { return sBar + 8u * (kStages + s); };
-    auto afull = [&](int t) { return sBar + 8u * (2 * kStages + t); };
-    auto aempty = [&](int t) { return sBar + 8u * (2 * kStages + kAbuf + t); };
-    auto dfull = [&](int q) { return sBar + 8u * (2 * kStages + 2 * kAbuf + q); };
-    auto dempty = [&](int q) { return sBar + 8u * (2 * kStages + 2 * kAbuf + 2 + q); };
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sbase + kBarOff + 384);
-    double* s_csum = reinterpret_cast<double*>(sbase + kBarOff + 392);     // [2]
-    long long* s_c = reinterpret_cast<long long*>(sbase + kBarOff + 512);  // [4 warps][2][kDigits]
+    uint8_t* sb = smem_raw + (base - raw);
+    const uint32_t sP = base, sD = base + kOffD, sG = base + kOffG, sBar = base + kOffBar;
+    auto pfull = [&](int i) { return sBar + 8u * i; };
+    auto pempty = [&](int i) { return sBar + 8u * (kRP + i); };
+    auto dfull = [&](int i) { return sBar + 8u * (2 * kRP + i); };
+    auto dempty = [&](int i) { return sBar + 8u * (2 * kRP + kRD + i); };
+    auto gfull = [&](int i) { return sBar + 8u * (2 * kRP + 2 * kRD + i); };
+    auto gempty = [&](int i) { return sBar + 8u * (2 * kRP + 2 * kRD + kRA + i); };
+    const uint32_t afull = sBar + 8u * (2 * kRP + 2 * kRD + 2 * kRA);
+    const uint32_t aempty = afull + 8u;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sb + kOffBar + 512);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(sm_addr(tmem_slot)),
-                     "r"(kTmemCols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
-    }
+    if (warp == 0) tc::tmem_alloc(sm_addr(tmem_slot), kTmemCols);
     if (threadIdx.x == 32) {
-        for (int s = 0; s < kStages; ++s) {
-            bar_init(full(s), 1);
-            bar_init(empty(s), 1);
+        for (int i = 0; i < kRP; ++i) {
+            bar_init(pfull(i), 1);
+            bar_init(pempty(i), kDecodeWarps + 1);  // decode warps and the digit warp
         }
-        for (int t = 0; t < kAbuf; ++t) {
-            bar_init(afull(t), kDecodeWarps);
-            bar_init(aempty(t), 1);
+        for (int i = 0; i < kRD; ++i) {
+            bar_init(dfull(i), 8);
+            bar_init(dempty(i), 1);
         }
-        for (int q = 0; q < 2; ++q) {
-            bar_init(dfull(q), 1);
-            bar_init(dempty(q), 4);
+        for (int i = 0; i < kRA; ++i) {
+            bar_init(gfull(i), 1);
+            bar_init(gempty(i), 1);
         }
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        bar_init(afull, 1);
+        bar_init(aempty, 1);
+        tc::bar_init_fence();
     }
-    tc_fence_before();
+    tc::fence_before();
     __syncthreads();
-    tc_fence_after();
+    tc::fence_after();
     const uint32_t tmem = *tmem_slot;
+    if (warp >= 4 && warp < 8) {
+        // every lane: block scales 1.0 (UE8M0 127) and zero digit buffers
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        uint32_t v[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0x7F7F7F7Fu;
+        tmem_st32(tmem + lane_base + kColSF, v);
+        tmem_st32(tmem + lane_base + kColSF + 32u, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0u;
+        for (int b = 0; b < kRA; ++b) tmem_st32(tmem + lane_base + kColA + 32u * b, v);
+        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
     const int nitems = a.ntiles * a.nranges;
     auto fail = [&](int code) { atomicCAS(a.err, 0, code); };
 
     if (warp == 0) {
-        // ---- copy producer: per stage one TMA box (packed) + one bulk copy (digits)
+        // ---- copies: per stage two TMA boxes (256 rows x 128 bytes) and the stage's z values
         if (lane == 0) {
-            uint32_t it = 0;
+            uint32_t ps = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
                 const int tile = item / a.nranges, range = item % a.nranges;
                 const int st0 = range * a.range_stages, nst = min(a.range_stages, a.nstages - st0);
-                for (int k = 0; k < nst; ++k, ++it) {
-                    const int s = (int)(it % kStages);
-                    if (!bar_wait(empty(s), ((it / kStages) & 1u) ^ 1u)) {
+                for (int k = 0; k < nst; ++k, ++ps) {
+                    const int s = (int)(ps % kRP);
+                    if (!bar_wait(pempty(s), ((ps / kRP) & 1u) ^ 1u)) {
                         fail(1);
                         ok = false;
                         break;
                     }
-                    bar_expect_tx(full(s), kPackedBytes + kDigitBytes);
-                    tma_2d(sPacked + s * kPackedBytes, &tmap, kStageRowBytes * (st0 + k), tile * kRows, full(s));
-                    bulk_g2s(sDig + s * kDigitBytes, a.dig + (size_t)(st0 + k) * kDigitBytes, kDigitBytes, full(s));
+                    bar_expect_tx(pfull(s), kStageBytes + kGBytes);
+                    const int x = 128 * (st0 + k);
+                    tma_2d(sP + s * kStageBytes, &tmap, x, kTile * tile, pfull(s));
+                    tma_2d(sP + s * kStageBytes + kBoxBytes, &tmap, x, kTile * tile + kBox, pfull(s));
+                    bulk_g2s(sG + s * kGBytes, a.image + (size_t)(st0 + k) * (2 * kDigitRows * kUnitWords), kGBytes,
+                             pfull(s));
                 }
             }
             // drain: every issued copy has landed before the CTA may exit
-            const uint32_t first = it > (uint32_t)kStages ? it - kStages : 0u;
-            for (uint32_t q = first; q < it; ++q)
-                if (!bar_wait(full((int)(q % kStages)), (q / kStages) & 1u)) fail(2);
+            for (uint32_t q = ps > (uint32_t)kRP ? ps - kRP : 0u; q < ps; ++q)
+                if (!bar_wait(pfull((int)(q % kRP)), (q / kRP) & 1u)) fail(2);
         }
-    } else if (warp == 1) {
-        // ---- MMA issuer: per stage 16 MMAs (class a, b x eight 32-byte K-steps) into 8 accumulators.
-        // The decode warps arrive on afull only after they have seen the stage's copies land.
+    } else if (warp == kWarpMma) {
+        // ---- MMA issuer: per K-chunk of 256 samples four MMAs (K = 64) into the one accumulator
         if (lane == 0) {
-            uint32_t it = 0, li = 0;
+            uint32_t du = 0, li = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++li) {
                 const int range = item % a.nranges;
                 const int st0 = range * a.range_stages, nst = min(a.range_stages, a.nstages - st0);
-                const uint32_t acc = li & 1u;
-                if (!bar_wait(dempty(acc), ((li >> 1) & 1u) ^ 1u)) {
+                if (!bar_wait(aempty, (li & 1u) ^ 1u)) {  // the epilogue has read the previous item
                     fail(3);
                     break;
                 }
-                tc_fence_after();
-                const uint32_t dbase = tmem + kColD + 128u * acc;
-                for (int k = 0; k < nst; ++k, ++it) {
-                    const int s = (int)(it % kStages), t = (int)(it % kAbuf);
-                    if (!bar_wait(afull(t), (it / kAbuf) & 1u)) {
+                tc::fence_after();
+                for (int g = 0; g < 2 * nst; ++g, ++du) {
+                    const int d = (int)(du % kRD), ga = (int)(du % kRA);
+                    if (!bar_wait(dfull(d), (du / kRD) & 1u) || !bar_wait(gfull(ga), (du / kRA) & 1u)) {
                         fail(4);
                         ok = false;
                         break;
                     }
-                    tc_fence_after();
-                    const uint32_t aA = tmem + 128u * t;
-                    const uint64_t d0 = desc_sw128(sDig + s * kDigitBytes);
+                    tc::fence_after();
+                    const uint64_t bd = desc_sw128(sD + d * kUnitBytes);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        // K-step i: 32 bytes = 8 columns; descriptor address in 16-byte units
-                        // (+2 per 32 bytes, +128 per 2 KB atom); atoms 0-1 class a, 2-3 class b
-                        const uint32_t acc_in = (k != 0) || (i >= 4);
-                        const uint64_t dd = d0 + (uint64_t)(128 * (i >> 2) + 2 * (i & 3));
-                        mma_e4m3_ts(dbase + 16u * (i & 3), aA + 8u * i, dd, acc_in);
-                        mma_e4m3_ts(dbase + 64u + 16u * (i & 3), aA + 64u + 8u * i, dd + 256, acc_in);
-                    }
-                    mma_commit(aempty(t));
-                    mma_commit(empty(s));
+                    for (int ks = 0; ks < 4; ++ks)
+                        mma_f4_ts(tmem, tmem + kColA + 32u * ga + 8u * ks, bd + 2 * ks, tmem + kColSFA,
+                                  tmem + kColSFB, (g | ks) != 0);
+                    mma_commit(dempty(d));
+                    mma_commit(gempty(ga));
                 }
-                if (ok) mma_commit(dfull(acc));
+                if (ok) mma_commit(afull);
             }
             // drain: the last commit covers every MMA issued by this thread
-            if (it > 0) {
-                const uint32_t q = it - 1;
-                if (!bar_wait(empty((int)(q % kStages)), (q / kStages) & 1u)) fail(5);
+            if (du > 0) {
+                const uint32_t q = du - 1;
+                if (!bar_wait(dempty((int)(q % kRD)), (q / kRD) & 1u)) fail(5);
             }
         }
-    } else if (warp < kEpiWarp0) {
-        // ---- decode: row = lane of this warp's TMEM sub-partition, 32-byte quarter q of the stage
-        const int sub = warp & 3, q = (warp - kDecodeWarp0) >> 2;
-        const int row = 32 * sub + lane;
-        const uint32_t lane_base = (uint32_t)(32 * sub) << 16;
-        uint32_t it = 0;
+    } else if (warp == kWarpDigits) {
+        // ---- digits: rows 0-10 of each K-chunk, from the stage's shared-memory copy into
+        // tensor memory (lanes 0-31; rows 11-31 zero)
+        uint32_t ps = 0, du = 0;
         bool ok = true;
         for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
             const int range = item % a.nranges;
             const int st0 = range * a.range_stages, nst = min(a.range_stages, a.nstages - st0);
-            for (int k = 0; k < nst; ++k, ++it) {
-                const int s = (int)(it % kStages), t = (int)(it % kAbuf);
-                if (!bar_wait(full(s), (it / kStages) & 1u)) {
-                    fail(6);
+            for (int k = 0; k < nst && ok; ++k, ++ps) {
+                const int s = (int)(ps % kRP);
+                if (!tc::bar_wait_warp(pfull(s), (ps / kRP) & 1u)) {
+                    fail(10);
                     ok = false;
                     break;
                 }
-                // 128-byte swizzle of the TMA tile: 16-byte chunk c of row r sits at chunk c ^ (r & 7)
-                const uint8_t* rp = sbase + s * kPackedBytes + row * kStageRowBytes;
-                const uint4 q0 = *reinterpret_cast<const uint4*>(rp + (((2 * q) ^ (row & 7)) << 4));
-                const uint4 q1 = *reinterpret_cast<const uint4*>(rp + (((2 * q + 1) ^ (row & 7)) << 4));
-                const uint32_t W[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-                uint32_t ha[16], hb[16];
+                for (int h = 0; h < 2; ++h, ++du) {
+                    const int ga = (int)(du % kRA);
+                    uint32_t v[32];
+                    if (lane < kDigitRows) {
+                        const uint4* src = reinterpret_cast<const uint4*>(sb + kOffG + s * kGBytes +
+                                                                          (h * kDigitRows + lane) * kUnitWords * 4);
 #pragma unroll
-                for (int w = 0; w < 8; ++w) {
-                    const uint32_t Wv = W[w], W4 = Wv >> 4;
-                    ha[2 * w] = (Wv & 0x03030303u) | 0x38383838u;
-                    ha[2 * w + 1] = (W4 & 0x03030303u) | 0x38383838u;
-                    hb[2 * w] = (Wv & 0x0C0C0C0Cu) | 0x30303030u;
-                    hb[2 * w + 1] = (W4 & 0x0C0C0C0Cu) | 0x30303030u;
+                        for (int c = 0; c < 8; ++c) {
+                            const uint4 q = src[c];
+                            v[4 * c] = q.x;
+                            v[4 * c + 1] = q.y;
+                            v[4 * c + 2] = q.z;
+                            v[4 * c + 3] = q.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) v[c] = 0u;
+                    }
+                    if (!tc::bar_wait_warp(gempty(ga), ((du / kRA) & 1u) ^ 1u)) {
+                        fail(6);
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after();
+                    tmem_st32(tmem + kColA + 32u * ga, v);
+                    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+                    tc::fence_before();
+                    __syncwarp();
+                    if (lane == 0) bar_arrive(gfull(ga));
                 }
-                if (!bar_wait(aempty(t), ((it / kAbuf) & 1u) ^ 1u)) {
-                    fail(7);
-                    ok = false;
-                    break;
-                }
-                const uint32_t col = tmem + lane_base + 128u * t + 16u * q;
-                tmem_st16(col, ha);
-                tmem_st16(col + 64u, hb);
-                asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
-                tc_fence_before();
                 __syncwarp();
-                if (lane == 0) bar_arrive(afull(t));
+                if (ok && lane == 0) bar_arrive(pempty(s));
+            }
+        }
+    } else if (warp == kWarpEpi) {
+        // ---- epilogue: lane p = digit row p; X_j = sum_p 8^(10-p) 2 F_p,j over lanes 0-15
+        uint32_t li = 0;
+        const double sc = ldexp(a.dsc[0], -30);
+        const int p = lane & 15, sh = 3 * (kDigitRows - 1 - lane);
+        for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++li) {
+            const int tile = item / a.nranges, range = item % a.nranges;
+            if (!tc::bar_wait_warp(afull, li & 1u)) {
+                fail(7);
+                break;
+            }
+            tc::fence_after();
+#pragma unroll 1
+            for (int g = 0; g < 8; ++g) {
+                uint32_t r[32];
+                tc::tmem_ld32(tmem + 32u * g, r);
+                if (g == 7) {
+                    tc::fence_before();
+                    __syncwarp();
+                    if (lane == 0) bar_arrive(aempty);
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    long long v[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        v[i] = lane < kDigitRows
+                                   ? (long long)__float2int_rn(2.f * __uint_as_float(r[16 * h + i])) << sh
+                                   : 0LL;
+                    bt_reduce_scatter<16>(v, p);
+                    const int64_t j = (int64_t)tile * kTile + 32 * g + 16 * h + p;
+                    if (lane < 16 && j < a.m) a.p1[(int64_t)range * a.m + j] = sc * (double)v[0];
+                }
             }
         }
     } else {
-        // ---- epilogue
-        const int sub = warp & 3, et = threadIdx.x - 32 * kEpiWarp0;
-        const uint32_t lane_base = (uint32_t)(32 * sub) << 16;
-        // class digit sums over all samples: s_csum[0] = sum_p 16^-(p+1) (S_a + S_b) = sum u~'/S,
-        // s_csum[1] = sum_p 16^-(p+1) (8 S_a + 2 S_b), the offsets of H_a and H_b, exactly
-        {
-            long long c[2][kDigits];
-#pragma unroll
-            for (int p = 0; p < kDigits; ++p) c[0][p] = c[1][p] = 0;
-            for (int st = et; st < a.nstages; st += 128)
-#pragma unroll
-                for (int p = 0; p < kDigits; ++p) {
-                    c[0][p] += a.cs[(size_t)st * 16 + p];
-                    c[1][p] += a.cs[(size_t)st * 16 + 8 + p];
+        // ---- decode: SNP row 32 (index mod 8) + lane of the tile, K-chunk h = index / 8 of every stage
+        const int di = decode_index(warp), h = di >> 3;
+        const int row = 32 * (di & 7) + lane, box = row >> 7, rr = row & 127;
+        uint32_t ps = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            const int range = item % a.nranges;
+            const int nst = min(a.range_stages, a.nstages - range * a.range_stages);
+            for (int k = 0; k < nst && ok; ++k, ++ps) {
+                const int s = (int)(ps % kRP);
+                if (!tc::bar_wait_warp(pfull(s), (ps / kRP) & 1u)) {
+                    fail(8);
+                    ok = false;
+                    break;
                 }
+                const uint8_t* prow = sb + s * kStageBytes + box * kBoxBytes + rr * 128;
+                const uint32_t du = 2 * ps + (uint32_t)h;  // this K-chunk's place in the sequence of all K-chunks
+                const int d = (int)(du % kRD);
+                uint4 P[4];
 #pragma unroll
-            for (int cl = 0; cl < 2; ++cl)
+                for (int c = 0; c < 4; ++c)
+                    P[c] = *reinterpret_cast<const uint4*>(prow + (((4 * h + c) ^ (rr & 7)) << 4));
+                if (!tc::bar_wait_warp(dempty(d), ((du / kRD) & 1u) ^ 1u)) {
+                    fail(9);
+                    ok = false;
+                    break;
+                }
+                uint8_t* drow = sb + kOffD + d * kUnitBytes + (row >> 3) * 1024 + (row & 7) * 128;
 #pragma unroll
-                for (int p = 0; p < kDigits; ++p) {
-                    long long v = c[cl][p];
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                    if (lane == 0) s_c[((warp - kEpiWarp0) * 2 + cl) * kDigits + p] = v;
-                }
-        }
-        asm volatile("bar.sync 1, 128;\n" ::: "memory");
-        if (et == 0) {
-            double t0 = 0.0, t1 = 0.0;
-            for (int p = kDigits - 1; p >= 0; --p) {
-                long long ca = 0, cb = 0;
-                for (int w = 0; w < 4; ++w) {
-                    ca += s_c[(w * 2 + 0) * kDigits + p];
-                    cb += s_c[(w * 2 + 1) * kDigits + p];
-                }
-                t0 += ldexp((double)(ca + cb), -4 * (p + 1));
-                t1 += ldexp((double)(8 * ca + 2 * cb), -4 * (p + 1));
-            }
-            s_csum[0] = t0;
-            s_csum[1] = t1;
-        }
-        asm volatile("bar.sync 1, 128;\n" ::: "memory");
-        const double S = a.dsc[0], usum = S * s_csum[0], hoff = S * s_csum[1];
-        uint32_t li = 0;
-        for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++li) {
-            const int tile = item / a.nranges, range = item % a.nranges;
-            const uint32_t acc = li & 1u;
-            if (!bar_wait(dfull(acc), (li >> 1) & 1u)) {
-                fail(8);
-                break;
-            }
-            tc_fence_after();
-            const int64_t j = (int64_t)tile * kRows + 32 * sub + lane;
-            double hs = 0.0;
-            {
-                uint32_t r[32];
+                for (int c = 0; c < 4; ++c) {
+                    const uint32_t W[4] = {P[c].x, P[c].y, P[c].z, P[c].w};
+                    uint32_t o[8];
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {  // accumulators 2h, 2h+1: class a (h < 2) or b
-                    tmem_ld32(tmem + lane_base + kColD + 128u * acc + 32u * h, r);
-                    const double wgt = h < 2 ? 8.0 : 4.0;
-#pragma unroll
-                    for (int p = kDigits - 1; p >= 0; --p)
-                        hs += ldexp(wgt, -4 * (p + 1)) *
-                              ((double)__uint_as_float(r[p]) + (double)__uint_as_float(r[16 + p]));
+                    for (int q = 0; q < 4; ++q) {
+                        o[2 * q] = W[q] & 0x33333333u;             // even samples: codes 0, 2 of each byte
+                        o[2 * q + 1] = (W[q] >> 2) & 0x33333333u;  // odd samples
+                    }
+                    *reinterpret_cast<uint4*>(drow + (((2 * c) ^ (row & 7)) << 4)) = make_uint4(o[0], o[1], o[2], o[3]);
+                    *reinterpret_cast<uint4*>(drow + (((2 * c + 1) ^ (row & 7)) << 4)) =
+                        make_uint4(o[4], o[5], o[6], o[7]);
                 }
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) bar_arrive(dempty(acc));
-            if (j < a.m) {
-                double P1 = S * hs, P3 = 0.0;
-                if (range == 0) {
-                    P1 -= hoff;                // the offsets of H_a and H_b over all samples
-                    P3 += a.dsc[2] - usum;     // so that sum u~ - sum_r p3 = sum_{obs} u~'
+                tc::fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) {
+                    bar_arrive(dfull(d));
+                    bar_arrive(pempty(s));
                 }
-                a.p1[(int64_t)range * a.m + j] = P1;
-                a.p3[(int64_t)range * a.m + j] = P3;
             }
         }
     }
-    tc_fence_before();
+    tc::fence_before();
     __syncthreads();
     if (warp == 0) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, kTmemCols);
     }
 }
 
-// ---- missing-code list (CSR) and the per-product gather ----------------------
+// ---- the list of missing codes and its per-product sum ------------------------
 
 // counts[j] = missing codes of SNP j among samples 0..n-1; one warp per SNP.
 __global__ void __launch_bounds__(256) k_miss_count(const uint8_t* __restrict__ packed, int64_t stride, int64_t n,
@@ -524,70 +550,62 @@ __global__ void __launch_bounds__(256) k_miss_fill(const uint8_t* __restrict__ p
     }
 }
 
-// Missing terms of A^T u (no cross-block synchronisation): eight lanes per SNP
-// j, four SNPs per warp, eight list entries in flight per lane (the kernel is
-// bound by memory latency times the number of warp waves).  Z_a, Z_b = sums of
-// z_i over the listed samples of class a (i even) and b (i odd), exact in 64-bit
-// integers; p3[j] += S 2^-28 (Z_a + Z_b) and, for the operand of k_rmv_tc
-// (affine in the code, so a missing code contributes 3/8 or 3/4 of z_i),
-// p1[j] -= S 2^-28 (3 Z_a + 4 Z_b) (range-0 partials).
-__global__ void __launch_bounds__(256) k_miss_gather(const int64_t* __restrict__ off, const uint32_t* __restrict__ idx,
-                                                      int64_t m, const int* __restrict__ z,
-                                                      const double* __restrict__ dsc, double* __restrict__ p1,
-                                                      double* __restrict__ p3, int affine) {
+// Z_j = sum of z_i over the listed missing samples of SNP j, exact in 64-bit
+// integers, as p3[j] = S 2^-30 Z_j.  Eight lanes per SNP, four SNPs per warp,
+// eight list entries in flight per lane (the kernel is bound by the latency
+// of its loads times the number of warp waves; z is L2-resident).
+__global__ void __launch_bounds__(256) k_miss_sum(const int64_t* __restrict__ off, const uint32_t* __restrict__ idx,
+                                                   int64_t m, int64_t nz, const int* __restrict__ z,
+                                                   const double* __restrict__ dsc, double* __restrict__ p3,
+                                                   int* __restrict__ err) {
     const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
     const int sl = threadIdx.x & 7;
-    long long za = 0, zb = 0;
+    long long zs = 0;
     if (j < m) {
         const int64_t e1 = off[j + 1];
         for (int64_t e = off[j] + sl; e < e1; e += 64) {
             uint32_t ii[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) ii[u] = e + 8 * u < e1 ? idx[e + 8 * u] : 0xFFFFFFFFu;
+            for (int q = 0; q < 8; ++q) ii[q] = e + 8 * q < e1 ? __ldg(idx + e + 8 * q) : 0xFFFFFFFFu;
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (ii[u] != 0xFFFFFFFFu) {
-                    const long long v = z[ii[u]];
-                    if (ii[u] & 1u)
-                        zb += v;
+            for (int q = 0; q < 8; ++q)
+                if (ii[q] != 0xFFFFFFFFu) {
+                    if (ii[q] < nz)
+                        zs += __ldg(z + ii[q]);
                     else
-                        za += v;
+                        atomicCAS(err, 0, 51);  // a listed sample outside the z array: skipped, reported
                 }
         }
     }
 #pragma unroll
-    for (int o = 4; o > 0; o >>= 1) {
-        za += __shfl_xor_sync(0xffffffffu, za, o);
-        zb += __shfl_xor_sync(0xffffffffu, zb, o);
-    }
-    if (j < m && sl == 0 && (za | zb)) {
-        const double zs = ldexp(dsc[0], -28);
-        if (affine) p1[j] -= zs * (double)(3 * za + 4 * zb);
-        p3[j] += zs * (double)(za + zb);
-    }
+    for (int o = 4; o > 0; o >>= 1) zs += __shfl_xor_sync(0xffffffffu, zs, o);
+    if (j < m && sl == 0) p3[j] = ldexp(dsc[0], -30) * (double)zs;
 }
 
 // ---- finishing kernel ----------------------------------------------------------
 
-// Final combination over sample blocks (fixed order), then the solver epilogue.
+// Sums over the K-ranges (fixed order), then
+//   x_j = d_j w_j [ (sum_r P1 - 3 sum_r P3) - mu_j (sum_i u~_i - sum_r P3) ]
+// (P1 = S 2^-30 sum c z over the range, missing codes counted as 3; P3 = the
+// missing samples' share), the subtraction of earlier basis vectors and the
+// solver's norm reduction.
 __global__ void __launch_bounds__(256) k_rmv_tc_fin(const double* __restrict__ p1, const double* __restrict__ p3,
-                                                     int nb, int64_t m, const double* __restrict__ mu,
-                                                     const double* __restrict__ d, const float* __restrict__ w,
-                                                     const double* __restrict__ dsc, float* __restrict__ x, FinArgs fa,
-                                                     Sv sv) {
+                                                    int nr, int64_t m, const double* __restrict__ mu,
+                                                    const double* __restrict__ d, const float* __restrict__ w,
+                                                    const double* __restrict__ dsc, float* __restrict__ x, FinArgs fa,
+                                                    Sv sv) {
     if (fa.role != ROLE_NONE && sv.sc->abort) return;
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double sq = 0.0;
     if (j < m) {
         double hsum = 0.0, msum = 0.0;
-        for (int b = 0; b < nb; ++b) {
-            hsum += p1[(int64_t)b * m + j];
-            msum += p3[(int64_t)b * m + j];
-        }
+        for (int r = 0; r < nr; ++r) hsum += p1[(int64_t)r * m + j];
+        msum = p3[j];
         double dw = d[j];
         if (w) dw *= (double)w[j];
-        const double obs = dsc[2] - msum;  // sum of u~ over observed samples
-        float val = (float)(dw * (hsum - mu[j] * obs));
+        const double obs_g = hsum - 3.0 * msum;  // sum of g u~ over the observed samples
+        const double obs = dsc[2] - msum;        // sum of u~ over the observed samples
+        float val = (float)(dw * (obs_g - mu[j] * obs));
         const float* W = static_cast<const float*>(fa.W);
         for (int q = 0; q < fa.nsub; ++q) val -= (float)fa.bcol[q] * W[j + (int64_t)q * fa.ldw];
         x[j] = val;
@@ -599,9 +617,9 @@ __global__ void __launch_bounds__(256) k_rmv_tc_fin(const double* __restrict__ p
     if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += s_w[q];
-        sv.partials[(int64_t)blockIdx.x * (GKL_MAX_ELL + 2)] = a;
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += s_w[q];
+        sv.partials[(int64_t)blockIdx.x * (GKL_MAX_ELL + 2)] = t;
     }
     if (!arrive_last(&sv.sc->counter)) return;
     __shared__ double s_tot;
@@ -613,9 +631,9 @@ __global__ void __launch_bounds__(256) k_rmv_tc_fin(const double* __restrict__ p
     if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = tt;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += s_w[q];
-        s_tot = a;
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += s_w[q];
+        s_tot = t;
     }
     __syncthreads();
     step_epilogue(sv, fa.role, fa.j, s_tot);
@@ -629,24 +647,24 @@ static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct TcPlan {
     int nstages, range_stages, nranges, ntiles, grid;
-    size_t dig_bytes, cs_bytes, z_bytes, part_bytes;
+    int64_t nwords;  // digit-image words of one row: K-chunks x 32
+    size_t img_bytes, z_bytes, part_bytes;
 };
 
+// Work items (256-SNP tile, K-range): K-ranges of at most 2,048 stages; more
+// ranges only where they even out the last wave of items over the SMs.
 static TcPlan plan_tc(const gkl_handle* h) {
     TcPlan p;
-    p.nstages = (int)((h->stride + kStageRowBytes - 1) / kStageRowBytes);
-    p.ntiles = (int)((h->m + kRows - 1) / kRows);
+    p.nstages = (int)((h->stride + 127) / 128);
+    p.ntiles = (int)((h->m + kTile - 1) / kTile);
     const int sms = std::max(1, h->num_sms);
     const int nr0 = (p.nstages + kMaxRangeStages - 1) / kMaxRangeStages;
-    // K-ranges: at most 64,000 samples each; more ranges only where they even out
-    // the last wave of work items over the SMs by a few percent
     int best = nr0;
     double best_eff = 0.0;
     for (int nr = nr0; nr <= std::min(p.nstages, nr0 + 7); ++nr) {
         const int rs = (p.nstages + nr - 1) / nr, nranges = (p.nstages + rs - 1) / rs;
         const double items = (double)p.ntiles * nranges;
-        const double waves = std::ceil(items / sms);
-        const double eff = items / (waves * sms);
+        const double eff = items / (std::ceil(items / sms) * sms);
         if (eff > best_eff + 0.03) {
             best_eff = eff;
             best = nr;
@@ -655,24 +673,23 @@ static TcPlan plan_tc(const gkl_handle* h) {
     p.range_stages = (p.nstages + best - 1) / best;
     p.nranges = (p.nstages + p.range_stages - 1) / p.range_stages;
     p.grid = (int)std::min<int64_t>((int64_t)p.ntiles * p.nranges, sms);
-    p.dig_bytes = (size_t)p.nstages * kDigitBytes;
-    p.cs_bytes = (size_t)p.nstages * 16 * sizeof(int);
+    p.nwords = (int64_t)2 * p.nstages * kUnitWords;
+    p.img_bytes = (size_t)2 * p.nstages * kDigitRows * kUnitWords * sizeof(uint32_t);
     p.z_bytes = (size_t)p.nstages * kStageSamples * sizeof(int);
-    p.part_bytes = 2 * (size_t)p.nranges * (size_t)h->m * sizeof(double);
+    p.part_bytes = ((size_t)p.nranges + 1) * (size_t)h->m * sizeof(double);  // P1 per K-range, P3
     return p;
 }
 
 size_t rmv_tc_scratch_bytes(const gkl_handle* h) {
     const TcPlan p = plan_tc(h);
-    return p.dig_bytes + al256(p.cs_bytes) + al256(p.z_bytes) + p.part_bytes + 256;
+    return al256(p.img_bytes) + al256(p.z_bytes) + p.part_bytes + 256;
 }
 
-
 // Prepares the tensor-core path for a handle: the TMA descriptor of the packed
-// matrix (128-byte x 128-row boxes, 128-byte swizzle), the kernel's shared-memory
-// limit and the list of missing codes per SNP.  Returns false (gkl_init then
-// fails: the FP32 A^T u has no other kernel) if the driver entry point or a
-// step is unavailable or the packed buffer is not 16-byte aligned.
+// matrix (128-byte x 128-row boxes, 128-byte swizzle) and the kernel's
+// shared-memory limit, and the list of missing codes per SNP.  Returns false (gkl_init then fails: the FP32 A^T u has
+// no other kernel) if the driver entry point or a step is unavailable or the
+// packed buffer is not 16-byte aligned.
 bool tc_prepare(gkl_handle* h) {
     if (h->tc_state != 0) return h->tc_state > 0;
     h->tc_state = -1;
@@ -686,7 +703,7 @@ bool tc_prepare(gkl_handle* h) {
     alignas(64) CUtensorMap map;
     const cuuint64_t gdim[2] = {(cuuint64_t)h->stride, (cuuint64_t)h->m};
     const cuuint64_t gstride[1] = {(cuuint64_t)h->stride};
-    const cuuint32_t box[2] = {(cuuint32_t)kStageRowBytes, (cuuint32_t)kRows};
+    const cuuint32_t box[2] = {128u, (cuuint32_t)kBox};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(h->packed), gdim, gstride, box,
                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -725,13 +742,13 @@ bool tc_prepare(gkl_handle* h) {
     return true;
 }
 
+// Scale pass, digit image, the MMA kernel and the finishing kernel.
 cudaError_t launch_rmatvec_tc(const gkl_handle* h, const float* u, float* x, void* scratch, const Sv* sv,
                               const FinArgs* fa, cudaEvent_t ev0, cudaEvent_t ev1, int* nlaunch) {
     const TcPlan p = plan_tc(h);
-    uint8_t* dig = static_cast<uint8_t*>(scratch);
-    int* cs = reinterpret_cast<int*>(dig + p.dig_bytes);
-    int* z = reinterpret_cast<int*>(reinterpret_cast<char*>(cs) + ((p.cs_bytes + 255) & ~(size_t)255));
-    double* p1 = reinterpret_cast<double*>(reinterpret_cast<char*>(z) + ((p.z_bytes + 255) & ~(size_t)255));
+    uint32_t* img = static_cast<uint32_t*>(scratch);
+    int* z = reinterpret_cast<int*>(reinterpret_cast<char*>(scratch) + al256(p.img_bytes));
+    double* p1 = reinterpret_cast<double*>(reinterpret_cast<char*>(z) + al256(p.z_bytes));
     double* p3 = p1 + (size_t)p.nranges * h->m;
     double* aux = h->aux;  // dsc[4] | counter | partials of the scale pass; error word at kAuxErrOffset
     double* dsc = aux;
@@ -740,22 +757,28 @@ cudaError_t launch_rmatvec_tc(const gkl_handle* h, const float* u, float* x, voi
     int* err = reinterpret_cast<int*>(reinterpret_cast<char*>(aux) + kAuxErrOffset);
     cudaStream_t st = h->stream;
     const int sblocks = std::min(2 * h->num_sms, (int)((h->n + 255) / 256));
+    GKL_DEBUG_SYNC(st, "before A^T u");
     k_u_scale<<<std::max(1, sblocks), 256, 0, st>>>(u, h->s, h->n, part, counter, dsc);
-    k_u_digits_tc<<<p.nstages, kStageSamples, 0, st>>>(u, h->s, h->n, dsc, dig, cs, z);
+    GKL_DEBUG_SYNC(st, "k_u_scale");
+    k_u_digits_f4<<<(unsigned)((p.nwords + 255) / 256), 256, 0, st>>>(u, h->s, h->n, p.nwords, dsc, img, z);
+    GKL_DEBUG_SYNC(st, "k_u_digits_f4");
     alignas(64) CUtensorMap map;
     memcpy(&map, h->tc_map, sizeof(map));
-    TcArgs a{dig, cs, p.nstages, p.range_stages, p.nranges, p.ntiles, h->m, dsc, p1, p3, err};
+    TcArgs a{img, p.nstages, p.range_stages, p.nranges, p.ntiles, h->m, dsc, p1, err};
     if (ev0) cudaEventRecord(ev0, st);
     k_rmv_tc<<<p.grid, kThreads, kSmemBytes, st>>>(map, a);
     if (ev1) cudaEventRecord(ev1, st);
-    k_miss_gather<<<(unsigned)((h->m * 8 + 255) / 256), 256, 0, st>>>(h->miss_off, h->miss_idx, h->m, z, dsc, p1,
-                                                                       p3, 1);
+    GKL_DEBUG_SYNC(st, "k_rmv_tc");
+    k_miss_sum<<<(unsigned)((h->m * 8 + 255) / 256), 256, 0, st>>>(h->miss_off, h->miss_idx, h->m,
+                                                                    (int64_t)p.nstages * kStageSamples, z, dsc, p3, err);
+    GKL_DEBUG_SYNC(st, "k_miss_sum");
     FinArgs f{};
     Sv s{};
     if (fa) f = *fa;
     if (sv) s = *sv;
     k_rmv_tc_fin<<<(unsigned)((h->m + 255) / 256), 256, 0, st>>>(p1, p3, p.nranges, h->m, h->mu, h->d, h->w, dsc, x,
-                                                                    f, s);
+                                                                  f, s);
+    GKL_DEBUG_SYNC(st, "k_rmv_tc_fin");
     if (nlaunch) *nlaunch = 5;
     return cudaGetLastError();
 }

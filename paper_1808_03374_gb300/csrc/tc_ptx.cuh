@@ -42,6 +42,13 @@ __device__ __forceinline__ bool bar_wait(uint32_t a, uint32_t par) {
     return true;
 }
 
+// The same wait taken by every lane of a warp, with one answer for the whole
+// warp (all lanes must call it): a lane whose wait completed still reports
+// failure if another lane's ran out, so the warp never splits on it.
+__device__ __forceinline__ bool bar_wait_warp(uint32_t a, uint32_t par) {
+    return __all_sync(0xffffffffu, bar_wait(a, par));
+}
+
 // 2-D tiled TMA load into shared memory, completing on mbarrier `bar`.
 __device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
     asm volatile(

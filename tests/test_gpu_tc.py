@@ -15,7 +15,8 @@ from tests.helpers import oracle_matrix, small_geno, to_dev
 
 pytestmark = pytest.mark.gpu
 
-# ragged tails in both directions; n = 70,000 spans two K-ranges of the kernel
+# ragged tails in both directions; n = 70,000 spans several K-ranges of the kernel (the plan splits rows
+# of few SNP tiles into ranges to fill the SMs)
 SHAPES = [(1, 1), (5, 3), (255, 129), (256, 128), (257, 300), (1000, 2000), (4099, 777), (70_000, 300)]
 
 
@@ -102,3 +103,22 @@ def test_tc_special_vectors(gk):
     x = h.rmatvec(torch.tensor(wide, device="cuda")).double().cpu().numpy()
     xo = M.rmatvec(wide.astype(np.float64))
     assert np.all(np.abs(x - xo) <= bound(M, wide.astype(np.float64), xo))
+
+
+def test_products_after_solves_that_grow_the_outputs(gk):
+    """Solves with growing k reallocate the handle's output buffers; the FP32
+    A^T u afterwards (which reads the handle's list of missing codes) still
+    matches the oracle."""
+    import torch
+    n, m = 2003, 3001
+    g = small_geno(n, m, miss=0.02, seed=83)
+    M = oracle_matrix(g)
+    h = handle(gk, g)
+    for k in (3, 6, 9):
+        assert h.svd(k=k, ell=24, precision="fp32", tol=1e-5, seed=1).converged
+    u = synth.normal_vec(31, 0, n).astype(np.float32)
+    for _ in range(2):
+        x = h.rmatvec(torch.tensor(u, device="cuda")).double().cpu().numpy()
+        xo = M.rmatvec(u.astype(np.float64))
+        assert np.all(np.abs(x - xo) <= bound(M, u.astype(np.float64), xo))
+    h.sync()
