@@ -1,12 +1,18 @@
 #!/usr/bin/env python
 """Benchmark: thick-restarted GKL on a GWAS-shaped packed genotype matrix.
 
-One step = one complete top-k solve (time-to-top-k at the stated residual) on
-the 10,000 samples x 100,000 SNPs workload (5-population admixture, 2%
-missing, 2-bit packed, 251 MB resident in HBM -- larger than L2, so no flush is
-needed between steps): FP32, partial reorthogonalisation, k=20, subspace 50,
-tol 1e-6.  The metric is matrix-vector pairs (A.v and A^T.u) per second over
-the whole job; ms_per_step is the time to top-k.
+Workload (N = 1): 200,000 samples x 1,000,000 SNPs, 20-population admixture,
+Beta(0.5, 2) base frequencies, 1% missing, 2-bit packed: 50 GB resident in
+HBM (far larger than L2, so no flush is needed between steps).  The matrix is
+drawn on the GPU by the seeded generator (byte for byte the C generator's).
+
+One step = one complete top-k solve (time-to-top-k at the stated residual):
+FP32 Lanczos vectors, reorthogonalisation with the adaptive second pass
+(DGKS), k = 20, subspace 50, tol 1e-6 -- plus the per-SNP weight gradient
+of sum_i sigma_i^2 from the solve's triplets.  The metric is matrix-vector
+pairs (A.v and A^T.u) per second over the whole job; ms_per_step is the time
+to top-k plus the gradient.  The true residuals of the timed solve are checked
+against tol with the library's 8-digit tensor-core block products.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -32,8 +38,11 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "fp32_pro_10k_x_100k"
+WORKLOAD = "large_200k_x_1m"
 METRIC = "GKL matvec-pairs/s and time-to-top-k at stated residual; HBM GB/s fraction"
+# oracle samples: the first SLAB_SNPS SNP rows of the workload (all samples),
+# drawn by the host generator (the same rows, byte for byte)
+SLAB_SNPS = 4000
 
 
 def dist_env():
@@ -60,6 +69,7 @@ def job_throughput(units_local: float, ms_local: float, dist=None, device="cpu")
 
 
 def measured_peaks():
+    """(HBM GB/s, source): the measured copy bandwidth, else the fallback."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
@@ -155,13 +165,6 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_inputs():
-    import synth
-    w = synth.CONFIGS[WORKLOAD]
-    g = synth.genotypes(w.geno)
-    return w, g
-
-
 def cpu_model() -> str:
     """The host CPU's model name as lscpu reports it ("" if unavailable)."""
     try:
@@ -174,14 +177,29 @@ def cpu_model() -> str:
     return ""
 
 
-def cpu_baseline_sample(w, g, budget_s=15.0, max_pairs=40):
-    """The FP64 oracle, as it stands, on a bounded sample of the same workload:
-    repeated A.v / A^T.u pairs over the full matrix (the per-step cost of GKL)."""
-    import numpy as np
+# ---- CPU oracle samples ------------------------------------------------------------
+
+def oracle_slab(w, snps: int = SLAB_SNPS):
+    """The first `snps` SNP rows of the workload (all samples), drawn by the
+    host generator -- the same bytes as those rows of the full matrix -- and
+    the oracle's operator over them."""
+    import dataclasses
+
     import oracle
     import synth
-    M = oracle.Matrix.from_packed(g.packed, g.n)
-    v = synth.normal_vec(77, 0, g.m)
+    spec = dataclasses.replace(w.geno, m=min(snps, w.geno.m))
+    g = synth.genotypes(spec)
+    return g, oracle.Matrix.from_packed(g.packed, g.n)
+
+
+def time_oracle_pairs(M, m_full: int, budget_s: float, max_pairs: int, seed: int = 77):
+    """Oracle A.v + A^T.u pairs on the slab until the budget is spent.
+    Returns (pairs, seconds, full-matrix pairs per second): a pair over the
+    slab reads M.m / m_full of the full matrix's entries."""
+    import numpy as np
+
+    import synth
+    v = synth.normal_vec(seed, 0, M.m)
     pairs, t0 = 0, time.perf_counter()
     while pairs < max_pairs:
         u = M.matvec(v)
@@ -192,57 +210,86 @@ def cpu_baseline_sample(w, g, budget_s=15.0, max_pairs=40):
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
+    return pairs, dt, pairs / dt * (M.m / m_full)
+
+
+def cpu_baseline_sample(w, budget_s=15.0, max_pairs=200):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload."""
+    g, M = oracle_slab(w)
+    pairs, dt, rate = time_oracle_pairs(M, w.geno.m, budget_s, max_pairs)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": pairs / dt, "unit": "pairs/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
-            "sample": f"{pairs} A.v + A^T.u pairs of the FP64 CPU oracle on the full {g.n} x {g.m} packed matrix "
-                      f"({dt:.1f} s)"}
+    return {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+            "sample": f"{pairs} A.v + A^T.u pairs of the FP64 CPU oracle over the first {M.m} of the {w.geno.m} "
+                      f"SNP rows (all {g.n} samples; {dt:.1f} s), scaled to the full matrix by {M.m}/{w.geno.m}"}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle on the host cores.  One step =
+    one oracle pair over the first SLAB_SNPS SNP rows; the value is scaled to
+    full-matrix pairs per second."""
+    import synth
     rank, _, world = dist_env()
     if rank != 0:
         return 0
-    w, g = make_inputs()
-    import numpy as np
-    import oracle
-    import synth
-    M = oracle.Matrix.from_packed(g.packed, g.n)
-    v = synth.normal_vec(77, 0, g.m)
+    w = synth.CONFIGS[WORKLOAD]
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     if world > 1:
         # the launcher gives every rank OMP_NUM_THREADS=1; rank 0 alone runs the
         # oracle here, on all host cores as at one GPU
         cores = os.cpu_count() or 1
         ctypes.CDLL("libgomp.so.1").omp_set_num_threads(cores)
-
-    def step():
-        nonlocal v
-        u = M.matvec(v)
-        u /= np.linalg.norm(u)
-        v = M.rmatvec(u)
-        v /= np.linalg.norm(v)
-
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    dt = time.perf_counter() - t0
-    val = args.steps / dt
-    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "pairs/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": g.n, "m": g.m, "step": "one A.v + A^T.u pair of the FP64 oracle"},
-            "cpu_baseline": {"value": val, "unit": "pairs/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
-                             "sample": f"{args.steps} oracle pairs on the full matrix"},
-            "e2e": {"value": val, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    g, M = oracle_slab(w)
+    time_oracle_pairs(M, w.geno.m, 1e9, max(0, args.warmup))
+    pairs, dt, rate = time_oracle_pairs(M, w.geno.m, 1e9, args.steps)
+    ms_full = 1e3 / rate
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "pairs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_full, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": w.geno.n, "m": w.geno.m,
+                       "step": f"one A.v + A^T.u pair of the FP64 oracle over the first {M.m} SNP rows, "
+                               f"reported per full-matrix pair ({w.geno.m} SNPs)"},
+            "cpu_baseline": {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+                             "sample": f"{pairs} oracle pairs over {M.m} of {w.geno.m} SNP rows ({dt:.1f} s)"},
+            "e2e": {"value": rate, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ---- the GPU arm -------------------------------------------------------------------
+
+def true_resid(h, res):
+    """max_i max(||A^T u_i - s_i v_i||, ||A v_i - s_i u_i||) / s_1 from the
+    library's 8-digit tensor-core block products (16 vectors per pass)."""
+    import torch
+    worst = 0.0
+    for c0 in range(0, res.U.shape[1], 16):
+        Ut = res.U[:, c0:c0 + 16].T.contiguous().float()
+        Vt = res.V[:, c0:c0 + 16].T.contiguous().float()
+        Z, Y = h.matmat(Ut, transpose=True), h.matmat(Vt)
+        sg = torch.tensor(res.sigma[c0:c0 + 16], device="cuda", dtype=torch.float32)[:, None]
+        worst = max(worst, torch.linalg.norm((Z - sg * Vt).double(), dim=1).max().item(),
+                    torch.linalg.norm((Y - sg * Ut).double(), dim=1).max().item())
+    return worst / res.sigma[0]
+
+
+def solve_kw(w, **extra):
+    return dict(k=w.k, ell=w.ell, reorth=w.reorth, precision=w.precision, tol=w.tol, maxit=3000, seed=7, **extra)
+
+
+def step_once(h, w, profile=False):
+    """One benchmark step: the top-k solve, then dL/dw for L = sum_i sigma_i^2
+    (the sigma part of the gradient, one A^T u per triplet).  Returns the
+    solve's result, the gradient and the pairs applied (an A^T u alone counts
+    as half a pair)."""
+    r = h.svd(profile=profile, **solve_kw(w))
+    _, gw = h.grad(sigma_bar=2.0 * r.sigma, want_s=False)
+    return r, gw, r.info["matvec_pairs"] + 0.5 * w.k
 
 
 def run_ours(args):
     import numpy as np
     import torch
+    import synth
     rank, local, world = dist_env()
     torch.cuda.set_device(local)
     pg = None
@@ -252,17 +299,18 @@ def run_ours(args):
         pg = dist
     from paper_1808_03374_gb300 import build, gkl
     build()
-    w, g = make_inputs()
-    packed_host = torch.from_numpy(g.packed).pin_memory()
-    packed = packed_host.to("cuda", non_blocking=False)
-    h = gkl.GKL(packed, g.n)
-    solve_kw = dict(k=w.k, ell=w.ell, reorth=w.reorth, precision=w.precision, tol=w.tol, maxit=2000, seed=7)
+    w = synth.CONFIGS[WORKLOAD]
+    n, m = w.geno.n, w.geno.m
+    t0 = time.time()
+    packed, _, _ = synth.genotypes_device(w.geno)
+    gen_s = time.time() - t0
+    h = gkl.GKL(packed, n)
+    stream = torch.cuda.current_stream()
 
     for _ in range(max(3, args.warmup)):
-        r = h.svd(**solve_kw)
+        step_once(h, w)
     torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
-    infos = []
+    infos, pairs = [], 0.0
     with ClockSampler(local) as clk:
         if pg:
             pg.barrier()
@@ -270,186 +318,148 @@ def run_ours(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            r = h.svd(profile=True, **solve_kw)
+            r, gw, p = step_once(h, w, profile=True)
             infos.append(r.info)
+            pairs += p
         e1.record(stream)
         torch.cuda.synchronize()
         if pg:
             pg.barrier()
-    pairs = sum(i["matvec_pairs"] for i in infos)
     value, ms = job_throughput(pairs, e0.elapsed_time(e1), pg, "cuda")
     clocks = clk.summary()
+    resid_true = true_resid(h, r)
 
-    # roofline of the dominant kernel, from the CUDA events recorded around each
-    # main product kernel during the timed solves
+    # roofline of the dominant kernel, from the CUDA events the library records
+    # around each main product kernel of the timed solves
     peak, peak_kind = measured_peaks()
-    n, m = g.n, g.m
     packed_bytes = m * ((n + 3) // 4)
+    kb = packed_bytes + 4 * m + 4 * n  # algorithmic bytes per launch: the packed matrix once + the two vectors
     mv_ms = sum(i["ms_mv"] for i in infos) / max(1, sum(i["n_mv"] for i in infos))
     rmv_ms = sum(i["ms_rmv"] for i in infos) / max(1, sum(i["n_rmv"] for i in infos))
-    tot_mv = sum(i["ms_mv"] for i in infos)
-    tot_rmv = sum(i["ms_rmv"] for i in infos)
-    # the FP32 path runs k_mv_pair (packed_ops.cu) and k_rmv_tc (packed_tc.cu; k_rmv_n256 with
-    # GKL_RMV_KERNEL=n256, k_rmv_mma in packed_mma.cu with GKL_RMV_KERNEL=mma); algorithmic bytes
-    # per launch = packed G once + the FP32 input and output vectors
-    rk = {"mma": ("k_rmv_mma", "packed_mma.cu"), "n256": ("k_rmv_n256", "packed_tc.cu")}.get(
-        os.environ.get("GKL_RMV_KERNEL", ""), ("k_rmv_tc", "packed_tc.cu"))
-    mv = ("k_mv_pair", "packed_ops.cu", mv_ms, packed_bytes + 4 * m + 4 * n)
-    rmv = (rk[0], rk[1], rmv_ms, packed_bytes + 4 * n + 4 * m)
-    dom, oth = (mv, rmv) if tot_mv >= tot_rmv else (rmv, mv)
-    kname, _, kms, kbytes = dom
-    achieved = kbytes / (kms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind,
-                "traffic": ncu_traffic(kname, WORKLOAD),
-                "algorithmic_bytes_per_launch": kbytes, "avg_launch_ms": kms,
-                "other_kernel": {oth[0]: {"avg_launch_ms": oth[2],
-                                          "achieved_gbs": oth[3] / (oth[2] / 1e3) / 1e9,
-                                          "traffic": ncu_traffic(oth[0], WORKLOAD)}},
-                "share_of_step": (tot_mv + tot_rmv) / ms}
+    tot_mv, tot_rmv = sum(i["ms_mv"] for i in infos), sum(i["ms_rmv"] for i in infos)
+    kern = {"k_mv_pair": {"file": "packed_ops.cu", "avg_launch_ms": mv_ms, "achieved_gbs": kb / mv_ms / 1e6,
+                          "frac": kb / mv_ms / 1e6 / peak, "total_ms_per_step": tot_mv / args.steps,
+                          "traffic": ncu_traffic("k_mv_pair", WORKLOAD)},
+            "k_rmv_tc": {"file": "packed_tc.cu", "avg_launch_ms": rmv_ms, "achieved_gbs": kb / rmv_ms / 1e6,
+                         "frac": kb / rmv_ms / 1e6 / peak, "total_ms_per_step": tot_rmv / args.steps,
+                         "traffic": ncu_traffic("k_rmv_tc", WORKLOAD)}}
+    dom = "k_mv_pair" if tot_mv >= tot_rmv else "k_rmv_tc"
+    oth = "k_rmv_tc" if dom == "k_mv_pair" else "k_mv_pair"
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                "frac": kern[dom]["frac"], "peak_source": peak_kind, "traffic": kern[dom]["traffic"],
+                "algorithmic_bytes_per_launch": kb, "avg_launch_ms": kern[dom]["avg_launch_ms"],
+                "other_kernel": {oth: kern[oth]}, "share_of_step": (tot_mv + tot_rmv) / ms}
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: the packed matrix
+    # from pinned host memory to the device, gkl_init (statistics, TMA views,
+    # missing-code lists), the solve with U and V copied to host memory, the
+    # gradient copied back
     e2e = None
     if not args.no_e2e:
-        e2e_steps = max(1, min(args.steps, 3))
+        host = torch.empty((m, packed.shape[1]), dtype=torch.uint8, pin_memory=True)
+        host.copy_(packed)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        e2e_pairs = 0
-        for _ in range(e2e_steps):
-            dev = packed_host.to("cuda", non_blocking=True)
+        e2e_pairs, d2h = 0.0, 0
+        for _ in range(args.e2e_steps):
+            dev = host.to("cuda", non_blocking=True)
             hh = gkl.GKL(dev, n)
-            rr = hh.svd(**solve_kw)
-            Uh = rr.U.cpu()
-            Vh = rr.V.cpu()
+            rr = hh.svd(out_host=True, **solve_kw(w))
+            _, gwe = hh.grad(sigma_bar=2.0 * rr.sigma, want_s=False)
+            gwh = gwe.cpu()
             hh.close()
-            e2e_pairs += rr.info["matvec_pairs"]
+            del dev
+            e2e_pairs += rr.info["matvec_pairs"] + 0.5 * w.k
+            d2h = (rr.U.numel() * rr.U.element_size() + rr.V.numel() * rr.V.element_size()
+                   + gwh.numel() * gwh.element_size() + 16 * w.k)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        e2e = {"value": job_throughput(e2e_pairs, dt * 1e3, pg, "cuda")[0], "unit": "pairs/s", "h2d_bytes_per_step": int(packed_host.numel()),
-               "d2h_bytes_per_step": int(Uh.numel() * Uh.element_size() + Vh.numel() * Vh.element_size() + 16 * w.k),
-               "steps": e2e_steps}
+        e2e = {"value": job_throughput(e2e_pairs, dt * 1e3, pg, "cuda")[0], "unit": "pairs/s",
+               "h2d_bytes_per_step": int(host.numel()), "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps}
+        del host
 
-    # block form (tensor-core block products) beside the FP32 solves (the timed
-    # PARTIAL one and one with FULL reorthogonalisation), timed separately: time
-    # to the converged top-k and the true residuals
-    # max_i max(||A^T u_i - s_i v_i||, ||A v_i - s_i u_i||) / s_1 from the
-    # library's own 8-digit block products
+    # block form (tensor-core block products, b = 16, subspace 128) beside the
+    # timed solve: time to the converged top-k and its true residual
     block_form = None
     if not args.no_block:
-        def true_resid(res):
-            Ut, Vt = res.U.T.contiguous(), res.V.T.contiguous()
-            Z, Y = h.matmat(Ut, transpose=True), h.matmat(Vt)
-            sgm = torch.tensor(res.sigma, device="cuda", dtype=torch.float32)[:, None]
-            ra = torch.linalg.norm((Z - sgm * Vt).double(), dim=1).max().item()
-            rb = torch.linalg.norm((Y - sgm * Ut).double(), dim=1).max().item()
-            return max(ra, rb) / res.sigma[0]
-        bkw = dict(k=w.k, ell=128, precision="block", block=16, k_keep=48, tol=w.tol, maxit=500, seed=7)
-        for _ in range(2):
-            rb_ = h.svd(**bkw)
+        bkw = dict(k=w.k, ell=w.extra["block_ell"], precision="block", block=w.extra["block"],
+                   k_keep=w.extra["k_keep"], tol=w.tol, maxit=500, seed=7, profile=True)
         torch.cuda.synchronize()
         b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        nb = 3
         b0.record(stream)
-        binfos = []
-        for _ in range(nb):
-            rb_ = h.svd(profile=True, **bkw)
-            binfos.append(rb_.info)
+        rb = h.svd(**bkw)
         b1.record(stream)
         torch.cuda.synchronize()
-        bms = b0.elapsed_time(b1) / nb
-        # tensor roofline of the block products: per launch 16 ceil(m/128) ceil(stride/128)
-        # MMAs of M=128, N=256, K=32 (e4m3); algorithmic FLOP 2 n m q with q = 16 vectors
-        stride = (g.n + 3) // 4
-        stride = (stride + 15) // 16 * 16
-        mmas = 16 * ((g.m + 127) // 128) * ((stride + 127) // 128)
-        issued = 2.0 * 128 * 256 * 32 * mmas
-        algo = 2.0 * g.n * g.m * 16
         tpeak, tsrc = measured_e4m3_peak()
+        stride = packed.shape[1]
+        mmas = 16 * ((m + 127) // 128) * ((stride + 127) // 128)  # MMAs of one 16-vector product
+        issued = 2.0 * 128 * 256 * 32 * mmas
         bt = {}
         for key, kn in (("rmv", "k_bt_rmv"), ("mv", "k_bt_mv")):
-            nl = sum(i["n_" + key] for i in binfos)
-            kms = sum(i["ms_" + key] for i in binfos) / max(1, nl)
+            nl = rb.info["n_" + key]
+            kms = rb.info["ms_" + key] / max(1, nl)
             bt[kn] = {"avg_launch_ms": kms, "launches": nl,
+                      "achieved_gbs": kb / kms / 1e6 if kms > 0 else None,
                       "achieved_issued_tflops": issued / (kms / 1e3) / 1e12 if kms > 0 else None,
-                      "achieved_algorithmic_tflops": algo / (kms / 1e3) / 1e12 if kms > 0 else None,
-                      "traffic": ncu_traffic(kn, WORKLOAD)}
-        dom_bt = max(bt, key=lambda x: bt[x]["avg_launch_ms"] * bt[x]["launches"])
-        a_ = bt[dom_bt]["achieved_issued_tflops"]
-        block_roofline = {"bound": "tensor", "kernel": dom_bt, "achieved": a_, "peak": tpeak, "unit": "TFLOP/s",
-                          "frac": a_ / tpeak if a_ else None, "peak_source": tsrc,
-                          "traffic": bt[dom_bt]["traffic"], "issued_flop_per_launch": issued,
-                          "algorithmic_flop_per_launch": algo, "kernels": bt}
-        # the FP32 single-vector solve with full reorthogonalisation: orthonormal
-        # bases, so its true residual follows its reported one
-        fkw = dict(solve_kw, reorth="full")
-        rf = h.svd(**fkw)
-        torch.cuda.synchronize()
-        b0.record(stream)
-        for _ in range(nb):
-            rf = h.svd(**fkw)
-        b1.record(stream)
-        torch.cuda.synchronize()
-        fms = b0.elapsed_time(b1) / nb
-        block_form = {"config": {"block": 16, "ell": 128, "k_keep": 48, "tol": w.tol, "digits": 8,
-                                 "products": "tcgen05 kind::f8f6f4 (k_bt_rmv, k_bt_mv)"},
-                      "time_to_topk_ms": bms, "vector_pairs": rb_.info["matvec_pairs"],
-                      "restarts": rb_.info["restarts"], "converged": bool(rb_.info["converged"]),
-                      "true_max_rel_resid": true_resid(rb_),
-                      "fp32_path": {"time_to_topk_ms": ms / args.steps, "true_max_rel_resid": true_resid(r),
-                                    "reported_max_rel_resid": infos[-1]["max_rel_resid"]},
-                      "fp32_full_reorth": {"time_to_topk_ms": fms, "vector_pairs": rf.info["matvec_pairs"],
-                                           "true_max_rel_resid": true_resid(rf),
-                                           "reported_max_rel_resid": rf.info["max_rel_resid"]},
-                      "sigma_max_rel_diff_vs_fp32": float(np.max(np.abs(rb_.sigma - r.sigma)) / r.sigma[0]),
-                      "roofline": block_roofline}
+                      "algorithmic_tflops_16_vectors": 2.0 * n * m * 16 / (kms / 1e3) / 1e12 if kms > 0 else None}
+        block_form = {"config": {"block": w.extra["block"], "ell": w.extra["block_ell"], "k_keep": w.extra["k_keep"],
+                                 "tol": w.tol, "digits": 8, "products": "tcgen05 kind::f8f6f4 (k_bt_rmv, k_bt_mv)"},
+                      "time_to_topk_ms": b0.elapsed_time(b1), "vector_pairs": rb.info["matvec_pairs"],
+                      "restarts": rb.info["restarts"], "converged": bool(rb.info["converged"]),
+                      "true_max_rel_resid": true_resid(h, rb),
+                      "sigma_max_rel_diff_vs_fp32": float(np.max(np.abs(rb.sigma - r.sigma) / r.sigma)),
+                      "peak_e4m3_tflops": tpeak, "peak_source": tsrc, "kernels": bt}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_sample(w, g)
+        cpu = cpu_baseline_sample(w)
 
     if rank != 0:
+        if pg:
+            pg.destroy_process_group()
         return 0
+    ms_step = ms / args.steps
     line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
-            "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "m": m, "k": w.k, "ell": w.ell, "reorth": w.reorth,
-                       "tol": w.tol, "precision": w.precision, "packed_bytes": int(g.packed.nbytes),
-                       "l2": "inputs larger than L2 (251 MB packed vs 129 MB L2); no flush",
-                       "parallelism": f"replicas x{world}"},
-            "time_to_topk_ms": ms / args.steps, "pairs_per_step": pairs / args.steps,
-            "max_rel_resid": infos[-1]["max_rel_resid"], "restarts": infos[-1]["restarts"],
-            "jacobi_sweeps": infos[-1]["jacobi_sweeps"], "svd_fallbacks": infos[-1]["svd_fallbacks"],
-            "svd_clusters": infos[-1]["svd_clusters"], "reorth_u": infos[-1]["reorth_u"],
+                       "tol": w.tol, "precision": w.precision, "packed_bytes": int(packed.numel()),
+                       "step": "top-k solve + per-SNP weight gradient of sum sigma_i^2",
+                       "l2": "inputs larger than L2 (50 GB packed vs 129 MB L2); no flush",
+                       "generated_on_device_s": gen_s, "parallelism": f"replicas x{world}"},
+            "time_to_topk_ms": sum(i["ms_total"] for i in infos) / args.steps,
+            "pairs_per_step": pairs / args.steps, "true_max_rel_resid": resid_true,
+            "reported_max_rel_resid": infos[-1]["max_rel_resid"], "restarts": infos[-1]["restarts"],
+            "reorth": {"u": infos[-1]["reorth_u"], "v": infos[-1]["reorth_v"], "second_u": infos[-1]["second_u"],
+                       "second_v": infos[-1]["second_v"]},
             "breakdown_ms_per_step": {
-                "A.v_main": sum(i["ms_mv"] for i in infos) / args.steps,
-                "A^T.u_main": sum(i["ms_rmv"] for i in infos) / args.steps,
+                "A.v_main": tot_mv / args.steps, "A^T.u_main": tot_rmv / args.steps,
                 "projected_svd": sum(i["ms_svd"] for i in infos) / args.steps,
                 "reorth": sum(i["ms_cgs"] for i in infos) / args.steps},
-            "reorth_v": infos[-1]["reorth_v"],
+            "sigma_top4": [float(x) for x in r.sigma[:4]],
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "block_form": block_form,
-            "gpu_launches": sum(i["launches"] for i in infos), "clocks": clocks}
+            "gpu_launches": sum(i["launches"] for i in infos) + args.steps * 7 * w.k, "clocks": clocks}
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
     return 0
 
 
-def run_block_profile(args):
-    """Two warm-up solves and one timed block-form solve at the benchmark
-    workload (for launch lists and kernel captures); prints one line."""
+def run_profile(args):
+    """Setup, then exactly one benchmark step (solve + gradient) on the
+    benchmark workload -- for profiler launch lists; prints one line."""
     import torch
+    import synth
     from paper_1808_03374_gb300 import build, gkl
     build()
-    w, g = make_inputs()
-    h = gkl.GKL(torch.from_numpy(g.packed).cuda(), g.n)
-    bkw = dict(k=w.k, ell=128, precision="block", block=16, k_keep=48, tol=w.tol, maxit=500, seed=7)
-    for _ in range(2):
-        r = h.svd(**bkw)
-    r = h.svd(**bkw)
+    w = synth.CONFIGS[args.profile_workload]
+    packed, _, _ = synth.genotypes_device(w.geno)
+    h = gkl.GKL(packed, w.geno.n)
     torch.cuda.synchronize()
-    print(json.dumps({"block_profile": WORKLOAD, "launches_per_solve": r.info["launches"],
-                      "ms": r.info["ms_total"], "vector_pairs": r.info["matvec_pairs"],
-                      "converged": r.info["converged"]}), flush=True)
+    r, _, pairs = step_once(h, w)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_step": args.profile_workload, "launches_solve": r.info["launches"],
+                      "ms_solve": r.info["ms_total"], "pairs": pairs}), flush=True)
     return 0
 
 
@@ -497,80 +507,6 @@ def run_paper_model(args):
                       "sigma_top10": [float(x) for x in ref.sigma[:k]], "runs": runs}), flush=True)
     return 0
 
-
-def run_compare(args):
-    """One workload of synth.CONFIGS: the FP32 single-vector solve (PARTIAL) and
-    the block form (b=16, l=128, k_keep=48), each once after the matrix is on
-    the device; times, pair counts, true residuals from the 8-digit block
-    products, singular-value agreement, and the sigma-part gradient
-    (d sum_i sigma_i^2 / dw) after the FP32 solve.  One JSON line."""
-    import numpy as np
-    import torch
-    import synth
-    from paper_1808_03374_gb300 import build, gkl
-    build()
-    w = synth.CONFIGS[args.compare]
-    t0 = time.time()
-    g = synth.genotypes(w.geno)
-    gen_s = time.time() - t0
-    t0 = time.time()
-    h = gkl.GKL(torch.from_numpy(g.packed).cuda(), g.n)
-    torch.cuda.synchronize()
-    init_s = time.time() - t0
-
-    def true_resid(res):
-        worst = 0.0
-        for c0 in range(0, res.U.shape[1], 16):  # 16 vectors per 8-digit pass
-            Ut = res.U[:, c0:c0 + 16].T.contiguous().float()
-            Vt = res.V[:, c0:c0 + 16].T.contiguous().float()
-            Z, Y = h.matmat(Ut, transpose=True), h.matmat(Vt)
-            sg = torch.tensor(res.sigma[c0:c0 + 16], device="cuda", dtype=torch.float32)[:, None]
-            worst = max(worst, torch.linalg.norm((Z - sg * Vt).double(), dim=1).max().item(),
-                        torch.linalg.norm((Y - sg * Ut).double(), dim=1).max().item())
-        return worst / res.sigma[0]
-
-    def timed(**kw):
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        r = h.svd(**kw)
-        torch.cuda.synchronize()
-        return time.perf_counter() - t, r
-
-    out = {"workload": args.compare, "n": g.n, "m": g.m, "packed_bytes": int(g.packed.nbytes),
-           "generated_s": gen_s, "to_device_and_init_s": init_s}
-    tb, rb = timed(k=w.k, ell=128, precision="block", block=16, k_keep=48, tol=1e-6, maxit=500, seed=7)
-    out["block"] = {"time_s": tb, "vector_pairs": int(rb.info["matvec_pairs"]), "restarts": int(rb.info["restarts"]),
-                    "converged": bool(rb.info["converged"]), "true_max_rel_resid": true_resid(rb)}
-    tf, rf = timed(k=w.k, ell=50, reorth="partial", precision="fp32", tol=1e-6, maxit=3000, seed=7)
-    out["fp32_partial"] = {"time_s": tf, "pairs": int(rf.info["matvec_pairs"]), "restarts": int(rf.info["restarts"]),
-                           "converged": bool(rf.info["converged"]), "reported_max_rel_resid": rf.info["max_rel_resid"],
-                           "true_max_rel_resid": true_resid(rf)}
-    out["sigma_max_rel_diff"] = float(np.max(np.abs(rb.sigma - rf.sigma)) / rf.sigma[0])
-    out["sigma_top5"] = [float(x) for x in rf.sigma[:5]]
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    _, gw = h.grad(sigma_bar=2.0 * rf.sigma, want_s=False, dtype=torch.float32)
-    torch.cuda.synchronize()
-    out["grad_w_sigma_part"] = {"time_s": time.perf_counter() - t, "norm": float(gw.double().norm().item())}
-    print(json.dumps({"compare": out}), flush=True)
-    return 0
-
-
-def run_fp32_profile(args):
-    """One FP32 solve of the benchmark step at the benchmark workload, right
-    after the handle is set up (for launch lists; no warm-up solves, so the
-    profiler skips only the set-up kernels); prints one line."""
-    import torch
-    from paper_1808_03374_gb300 import build, gkl
-    build()
-    w, g = make_inputs()
-    h = gkl.GKL(torch.from_numpy(g.packed).cuda(), g.n)
-    torch.cuda.synchronize()
-    r = h.svd(k=w.k, ell=w.ell, reorth=w.reorth, precision=w.precision, tol=w.tol, maxit=2000, seed=7)
-    torch.cuda.synchronize()
-    print(json.dumps({"fp32_profile": WORKLOAD, "launches_per_solve": r.info["launches"],
-                      "ms": r.info["ms_total"], "pairs": r.info["matvec_pairs"]}), flush=True)
-    return 0
 
 
 def run_cpu_pairs(args):
@@ -640,11 +576,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-block", action="store_true", help="skip the block-form comparison")
-    ap.add_argument("--profile-block", action="store_true",
-                    help="only warm up and run one block-form solve (for profiler launch lists)")
-    ap.add_argument("--profile-fp32", action="store_true",
-                    help="only set up and run one FP32 solve of the benchmark step (for profiler launch lists)")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-block", action="store_true", help="skip the block-form solve")
+    ap.add_argument("--profile", action="store_true",
+                    help="only set up and run one benchmark step (for profiler launch lists)")
+    ap.add_argument("--profile-workload", default=WORKLOAD, help=argparse.SUPPRESS)
     ap.add_argument("--paper-model", action="store_true",
                     help="the paper's synthetic model at its Table 3 size: solvers side by side (one JSON line)")
     ap.add_argument("--cpu-table", action="store_true",
@@ -654,19 +590,13 @@ def main():
     ap.add_argument("--cpu-threads", type=int, default=os.cpu_count() or 1, help=argparse.SUPPRESS)
     ap.add_argument("--max-pairs", type=int, default=3, help=argparse.SUPPRESS)
     ap.add_argument("--budget", type=float, default=20.0, help=argparse.SUPPRESS)
-    ap.add_argument("--compare", default=None,
-                    help="a workload of synth.CONFIGS: FP32 solve and block form side by side (one JSON line)")
     args = ap.parse_args()
-    if args.compare:
-        return run_compare(args)
     if args.cpu_table:
         return run_cpu_table(args)
     if args.cpu_pairs:
         return run_cpu_pairs(args)
-    if args.profile_block:
-        return run_block_profile(args)
-    if args.profile_fp32:
-        return run_fp32_profile(args)
+    if args.profile:
+        return run_profile(args)
     if args.paper_model:
         return run_paper_model(args)
     if args.impl == "reference":

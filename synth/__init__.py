@@ -306,7 +306,8 @@ CONFIGS = {
         "large_200k_x_1m",
         GenoSpec(n=200_000, m=1_000_000, n_pops=20, admixture=True,
                  base=("beta", 0.5, 2.0, 0.01, 0.5), miss_rate=0.01, seed=0x5EED0005),
-        k=20, ell=128, reorth="full", precision="block", tol=1e-6, extra={"block": 16, "k_keep": 48}),
+        k=20, ell=50, reorth="dgks", precision="fp32", tol=1e-6,
+        extra={"block": 16, "block_ell": 128, "k_keep": 48, "grad": "w"}),
 }
 
 
