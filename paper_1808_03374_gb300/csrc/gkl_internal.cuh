@@ -184,8 +184,9 @@ cudaError_t launch_scores(cudaStream_t st, int prec, const void* U, const double
 // list of missing codes once per handle.
 bool tc_prepare(gkl_handle* h);
 size_t rmv_tc_scratch_bytes(const gkl_handle* h);
-cudaError_t launch_rmatvec_tc(const gkl_handle* h, const float* u, float* x, void* scratch, const Sv* sv,
-                              const FinArgs* fa, cudaEvent_t ev0, cudaEvent_t ev1, int* nlaunch);
+template <typename T>
+cudaError_t launch_rmatvec_tc(const gkl_handle* h, const T* u, T* x, void* scratch, const Sv* sv, const FinArgs* fa,
+                              cudaEvent_t ev0, cudaEvent_t ev1, int* nlaunch);
 
 bool make_mv_map(const uint8_t* packed, int64_t stride, int64_t m, void* out);
 cudaError_t launch_colstats(const uint8_t* packed, int64_t n, int64_t m, int64_t stride, double* mu, double* scale,

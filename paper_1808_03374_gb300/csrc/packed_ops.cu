@@ -142,9 +142,8 @@ MvPlan plan_products(const gkl_handle* h) {
         }
     }
     size_t mv = (size_t)std::max(p.chunks, p.pair_chunks) * (size_t)p.ldp + (size_t)h->m * 4;  // partials + LUT
-    size_t rmv = 2 * (size_t)p.tiles * (size_t)h->m;
     size_t tc = h->tc_state > 0 ? rmv_tc_scratch_bytes(h) : 0;
-    p.bytes_fp64 = std::max(std::max(mv, rmv) * sizeof(double) + 256, tc);
+    p.bytes_fp64 = std::max(mv * sizeof(double) + 256, tc);
     return p;
 }
 
@@ -228,7 +227,6 @@ __global__ void __launch_bounds__(kThreads) k_mv_part(const uint8_t* __restrict_
 constexpr int kPairBatch = 128;                  // row pairs per table batch
 constexpr int kPairRows = 2 * kPairBatch;        // 256 rows
 constexpr int kPairTab = kPairBatch * 16;        // floats per table buffer (8 KB)
-constexpr int kPairMaxThreads = 256;
 
 template <int OFF>
 __device__ __forceinline__ float lds_f32(uint32_t a) {
@@ -523,124 +521,11 @@ cudaError_t launch_matvec(const gkl_handle* h, const T* v, T* y, void* scratch, 
 
 // ------------------------------------------------------------------ A^T u
 
-// Partial sums for x_j = d_j w_j [ sum_obs g_ij u~_i - mu_j sum_obs u~_i ],
-// u~ = s o u.  Each thread holds u~ for its 16 samples in registers and
-// streams the SNP rows of its chunk; the two sums are reduced across the
-// warp by shuffles and across warps in shared memory.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_rmv_part(const uint8_t* __restrict__ packed, int64_t stride, int64_t n,
-                                                       int64_t nwords, int64_t m, int rpc, const T* __restrict__ u,
-                                                       const float* __restrict__ s, T* __restrict__ p1,
-                                                       T* __restrict__ p3) {
-    __shared__ T red1[kThreads / 32][kRowBatch + 1];
-    __shared__ T red3[kThreads / 32][kRowBatch + 1];
-    const int64_t word = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    const bool active = word < nwords;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    T ut[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        int64_t i = word * 16 + k;
-        T val = (T)0;
-        if (active && i < n) val = s ? (T)s[i] * u[i] : u[i];
-        ut[k] = val;
-    }
-    const int64_t j0 = (int64_t)blockIdx.y * rpc;
-    const int64_t j1 = min(m, j0 + (int64_t)rpc);
-    const int64_t wstride = stride >> 2;
-    const uint32_t* base = reinterpret_cast<const uint32_t*>(packed) + (active ? word : 0);
-    for (int64_t jb = j0; jb < j1; jb += kRowBatch) {
-        const int nr = (int)min((int64_t)kRowBatch, j1 - jb);
-        for (int r = 0; r < nr; ++r) {
-            uint32_t wq = active ? __ldg(base + (jb + r) * wstride) : 0xFFFFFFFFu;
-            T a1 = (T)0, a3 = (T)0;
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                uint32_t c = (wq >> (2 * k)) & 3u;
-                T hv = (c == 3u) ? (T)0 : (T)c;
-                T ov = (c == 3u) ? (T)0 : (T)1;
-                a1 += hv * ut[k];
-                a3 += ov * ut[k];
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-                a3 += __shfl_xor_sync(0xffffffffu, a3, o);
-            }
-            if (lane == 0) {
-                red1[wid][r] = a1;
-                red3[wid][r] = a3;
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x < nr) {
-            T t1 = (T)0, t3 = (T)0;
-#pragma unroll
-            for (int q = 0; q < kThreads / 32; ++q) {
-                t1 += red1[q][threadIdx.x];
-                t3 += red3[q][threadIdx.x];
-            }
-            p1[(int64_t)blockIdx.x * m + jb + threadIdx.x] = t1;
-            p3[(int64_t)blockIdx.x * m + jb + threadIdx.x] = t3;
-        }
-        __syncthreads();
-    }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_rmv_fin(const T* __restrict__ p1, const T* __restrict__ p3, int tiles,
-                                                      int64_t m, const double* __restrict__ mu,
-                                                      const double* __restrict__ d, const float* __restrict__ w,
-                                                      T* __restrict__ x, FinArgs fa, Sv sv) {
-    if (fa.role != ROLE_NONE && sv.sc->abort) return;
-    const int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    double sq = 0.0;
-    if (j < m) {
-        T s1 = (T)0, s3 = (T)0;
-        for (int t = 0; t < tiles; ++t) {
-            s1 += p1[(int64_t)t * m + j];
-            s3 += p3[(int64_t)t * m + j];
-        }
-        double dw = d[j];
-        if (w) dw *= (double)w[j];
-        T val = (T)(dw * ((double)s1 - mu[j] * (double)s3));
-        const T* W = static_cast<const T*>(fa.W);
-        for (int q = 0; q < fa.nsub; ++q) val -= (T)fa.bcol[q] * W[j + (int64_t)q * fa.ldw];
-        x[j] = val;
-        sq = (double)val * (double)val;
-    }
-    if (fa.role == ROLE_NONE) return;
-    block_sum_to(sq, sv.partials + (int64_t)blockIdx.x * (GKL_MAX_ELL + 2));
-    if (arrive_last(&sv.sc->counter)) finish_norm(sv, fa.role, fa.j);
-}
-
+// Both precisions run the tensor-core kernel (gkl_init fails without it).
 template <typename T>
 cudaError_t launch_rmatvec(const gkl_handle* h, const T* u, T* x, void* scratch, const Sv* sv, const FinArgs* fa,
                            cudaEvent_t ev0, cudaEvent_t ev1, int* nlaunch) {
-    if constexpr (sizeof(T) == sizeof(float)) {
-        // FP32: the tensor-core kernel is the only FP32 A^T u (gkl_init fails without it)
-        if (h->tc_state <= 0) return cudaErrorNotSupported;
-        return launch_rmatvec_tc(h, reinterpret_cast<const float*>(u), reinterpret_cast<float*>(x), scratch, sv, fa,
-                                 ev0, ev1, nlaunch);
-    } else {
-        MvPlan p = plan_products(h);
-        T* p1 = static_cast<T*>(scratch);
-        T* p3 = p1 + (size_t)p.tiles * (size_t)h->m;
-        cudaStream_t st = h->stream;
-        dim3 grid((unsigned)p.tiles, (unsigned)p.chunks);
-        if (ev0) cudaEventRecord(ev0, st);
-        k_rmv_part<T><<<grid, kThreads, 0, st>>>(h->packed, h->stride, h->n, p.nwords, h->m, p.rows_per_chunk, u, h->s,
-                                                 p1, p3);
-        if (ev1) cudaEventRecord(ev1, st);
-        if (nlaunch) *nlaunch = 2;
-        FinArgs f{};
-        Sv s{};
-        if (fa) f = *fa;
-        if (sv) s = *sv;
-        k_rmv_fin<T><<<(unsigned)((h->m + kThreads - 1) / kThreads), kThreads, 0, st>>>(p1, p3, p.tiles, h->m, h->mu,
-                                                                                        h->d, h->w, x, f, s);
-        return cudaGetLastError();
-    }
+    return launch_rmatvec_tc<T>(h, u, x, scratch, sv, fa, ev0, ev1, nlaunch);
 }
 
 template cudaError_t launch_matvec<float>(const gkl_handle*, const float*, float*, void*, const Sv*, const FinArgs*,

@@ -1,4 +1,4 @@
-// Blackwell tensor-core A^T u for the FP32 path:
+// Blackwell tensor-core A^T u (FP32 and FP64 paths):
 //     x_j = d_j w_j [ sum_{i obs} g_ij u~_i - mu_j sum_{i obs} u~_i ],  u~ = s o u
 // (A as defined in gkl.h; the per-step product of GKL bidiagonalisation,
 // section 3 of arXiv:1808.03374).
@@ -6,12 +6,13 @@
 // The contraction over samples is exact integer arithmetic on the
 // 5th-generation tensor cores (tcgen05.mma kind::mxf4: packed e2m1 operands,
 // block scales all 1.0, FP32 accumulation in tensor memory):
-//  * u~ in fixed point: z_i = rint(u~_i 2^30 / S), S = 2^e >= max|u~|, so
-//    |z_i| <= 2^30 and u~'_i = S 2^-30 z_i is within 2^-31 S of u~_i; z_i is
-//    written with 11 balanced base-8 digits delta_p in [-4, 3] (all exact in
-//    e2m1), z_i = sum_p delta_p,i 8^(10-p);
-//  * orientation: the 11 digit rows are the MMA's A operand (M = 128 lanes of
-//    tensor memory, rows 11-127 zero), the codes of 256 SNPs its B operand
+//  * u~ in fixed point: z_i = rint(u~_i 2^b / S), S = 2^e > max|u~|, so
+//    |z_i| <= 2^b and u~'_i = S 2^-b z_i is within 2^-(b+1) S of u~_i; z_i is
+//    written with D = b/3 + 1 balanced base-8 digits delta_p in [-4, 3] (all
+//    exact in e2m1), z_i = sum_p delta_p,i 8^(D-1-p).  FP32: b = 30, D = 11;
+//    FP64: b = 57, D = 20 -- the same MMAs, more digit rows;
+//  * orientation: the D digit rows are the MMA's A operand (M = 128 lanes of
+//    tensor memory, the other rows zero), the codes of 256 SNPs its B operand
 //    (N = 256) and the samples its K axis: one MMA covers 256 SNPs x 64
 //    samples.  A 2-bit code c read as an e2m1 nibble is the value c/2, so the
 //    decode of a 32-bit word of 16 codes is two masks -- the 8 even samples
@@ -20,14 +21,14 @@
 //    image is written in that order);
 //  * accumulators F_p,j = sum_i (c_ij / 2) delta_p,i are multiples of 1/2
 //    below 2^23 (K-ranges of at most 2,048 stages of 512 samples), so exact in
-//    FP32, and X_j = sum_p 8^(10-p) 2 F_p,j = sum_i c_ij z_i is recombined in
-//    64-bit integers;
+//    FP32, and X_j = sum_p 8^(D-1-p) 2 F_p,j = sum_i c_ij z_i is recombined in
+//    64-bit integers (for D = 20 in two halves of 10 digits, joined in FP64);
 //  * the missing code 3 counts as 3 there.  The missing codes are few (1-2%
 //    of the entries) and fixed per matrix: gkl_init lists them once per SNP
 //    (sample indices, ascending) and a gather kernel forms Z_j = sum of z_i
 //    over the missing samples of SNP j (exact, 64-bit), so that
-//    sum_{obs} g u~' = S 2^-30 (X_j - 3 Z_j) and
-//    sum_{obs} u~' = sum_i u~'_i - S 2^-30 Z_j.  (Summing them in the decode
+//    sum_{obs} g u~' = S 2^-b (X_j - 3 Z_j) and
+//    sum_{obs} u~' = sum_i u~'_i - S 2^-b Z_j.  (Summing them in the decode
 //    warps instead costs a divergent loop per code word: measured 44 warp
 //    instructions per word, four times the MMAs' time.)
 // Data movement per 512-sample stage of a 256-SNP tile: two TMA boxes of
@@ -66,25 +67,43 @@ constexpr int kBoxBytes = kBox * 128;      // 16 KB
 constexpr int kStageBytes = 2 * kBoxBytes; // 32 KB of packed codes per stage
 constexpr int kUnitBytes = kTile * 128;    // decoded K-chunk: 256 rows x 128 bytes (256 samples in e2m1)
 constexpr int kRP = 3, kRD = 3, kRA = 3;   // ring depths: packed stages, decoded K-chunks, digit buffers
-constexpr int kDigitRows = 11;
-constexpr int kUnitWords = 32;             // tensor-memory columns of one K-chunk of digits (8 nibbles each)
+constexpr int kUnitWords = 32;
+constexpr int kDigitsF32 = 11, kDigitsF64 = 20;             // tensor-memory columns of one K-chunk of digits (8 nibbles each)
 constexpr int kMaxRangeStages = 2048;      // |2 F_p| <= 12 x 512 x 2048 < 2^24
 constexpr int kDecodeWarps = 16;           // two groups of 8: K-chunk 0 and 1 of every stage
 constexpr int kThreads = 640;              // 20 warps
 constexpr int kWarpMma = 1, kWarpDigits = 4, kWarpEpi = 8;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kColA = 256, kColSF = 448, kColSFA = 448, kColSFB = 480;
-constexpr int kGBytes = 2 * kDigitRows * kUnitWords * 4;  // digit rows of one stage (2 K-chunks), 2,816 bytes
 constexpr int kOffD = kRP * kStageBytes;
 constexpr int kOffG = kOffD + kRD * kUnitBytes;
-constexpr int kOffBar = kOffG + kRP * kGBytes;
-constexpr int kSmemBytes = 1024 + kOffBar + 1024;
 static_assert(kOffD % 1024 == 0, "decoded tiles must stay 1024-byte aligned");
-static_assert(kSmemBytes <= 232448, "shared memory of k_rmv_tc");
 // block-scaled instruction descriptor (kind::mxf4): A and B E2M1 (format 1,
 // bits 7-9 and 10-12), K-major, N >> 3 at bits 17-22, scale format UE8M0
 // (bit 23), M >> 4 at bits 24-28, scale-factor ids 0, K = 64 (bit 31 clear)
 constexpr uint32_t kIdesc = (1u << 7) | (1u << 10) | ((uint32_t)(kTile >> 3) << 17) | (1u << 23) | ((128u >> 4) << 24);
+
+// Fixed point with D balanced base-8 digits: z_i = rint(u~_i 2^kBits / S),
+// |z_i| <= 2^kBits = 8^(D-1) (the leading digit is then -1, 0 or 1).  D = 11
+// (30 bits, finer than FP32) serves the FP32 product, D = 20 (57 bits, finer
+// than FP64) the FP64 one.  Digit rows 0 .. kHalf0-1 sit in tensor-memory
+// lanes 0 .. kHalf0-1, the rest from lane 16 on, so that each 16-lane half
+// recombines its digits in 64-bit integers without overflow (weights at most
+// 8^10 on FP32 accumulators below 2^24).
+template <int D>
+struct Fx {
+    static constexpr int kBits = 3 * (D - 1);
+    static constexpr int kHalf0 = D <= 11 ? D : D / 2;
+    static constexpr int kGBytes = 2 * D * kUnitWords * 4;  // digit rows of one stage (2 K-chunks)
+    static constexpr int kOffBar = kOffG + kRP * kGBytes;
+    static constexpr int kSmem = 1024 + kOffBar + 1024;
+    static_assert(kSmem <= 232448, "shared memory of k_rmv_tc");
+    static_assert(D - kHalf0 <= 11 && kHalf0 <= 11, "weights of at most 8^10 per half");
+    // digit row held by tensor-memory lane L (0..31) of the digit warp, or -1
+    __host__ __device__ static constexpr int digit_of_lane(int L) {
+        return L < 16 ? (L < kHalf0 ? L : -1) : (L - 16 < D - kHalf0 ? kHalf0 + L - 16 : -1);
+    }
+};
 
 // decode warps: 2, 3, 5, 6, 7, 9 .. 19 -> index 0..15; index / 8 = the K-chunk of
 // every stage the warp decodes, 32 (index mod 8) + lane = its SNP row
@@ -129,7 +148,8 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32
 
 // Pass 1: max|u~| and sum u~ (FP64), combined by the last block; the scale
 // S = 2^e >= max|u~| and the sum go to dsc[0..2] = {S, 1/S, sum}.
-__global__ void __launch_bounds__(256) k_u_scale(const float* __restrict__ u, const float* __restrict__ s, int64_t n,
+template <typename T>
+__global__ void __launch_bounds__(256) k_u_scale(const T* __restrict__ u, const float* __restrict__ s, int64_t n,
                                                   double* __restrict__ part, unsigned* __restrict__ counter,
                                                   double* __restrict__ dsc) {
     double mx = 0.0, sm = 0.0;
@@ -181,19 +201,20 @@ __device__ __forceinline__ uint32_t e2m1_digit(int dg) {
 // One thread per tensor-memory word of a K-chunk (256 samples): the 8 samples
 // at K positions 8 w .. 8 w + 7 (K position kk of sample loc in the chunk:
 // 16 (loc / 16) + even/odd order within the 16, as the decode emits it).
-// Writes their z values and, for every digit row p < 11, the word of 8
+// Writes their z values and, for every digit row p < D, the word of 8
 // nibbles: image[chunk][p][w].
-__global__ void __launch_bounds__(256) k_u_digits_f4(const float* __restrict__ u, const float* __restrict__ s,
-                                                      int64_t n, int64_t nwords, const double* __restrict__ dsc,
-                                                      uint32_t* __restrict__ image, int* __restrict__ zout) {
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_u_digits_f4(const T* __restrict__ u, const float* __restrict__ s, int64_t n,
+                                                      int64_t nwords, const double* __restrict__ dsc,
+                                                      uint32_t* __restrict__ image, long long* __restrict__ zout) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nwords) return;
     const int64_t chunk = t / kUnitWords;
     const int w = (int)(t % kUnitWords);
     const double inv = dsc[1];
-    uint32_t word[kDigitRows];
+    uint32_t word[D];
 #pragma unroll
-    for (int p = 0; p < kDigitRows; ++p) word[p] = 0u;
+    for (int p = 0; p < D; ++p) word[p] = 0u;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
         const int kk = 8 * w + e;
@@ -201,36 +222,39 @@ __global__ void __launch_bounds__(256) k_u_digits_f4(const float* __restrict__ u
         const int64_t i = chunk * 256 + loc;
         long long z = 0;
         if (i < n) {
-            const double x = (double)u[i] * (s ? (double)s[i] : 1.0) * inv;  // |x| <= 1
-            z = __double2ll_rn(ldexp(x, 30));
+            const double x = (double)u[i] * (s ? (double)s[i] : 1.0) * inv;  // |x| < 1
+            z = __double2ll_rn(ldexp(x, Fx<D>::kBits));
         }
-        zout[i] = (int)z;
+        zout[i] = z;
         long long r = z;
 #pragma unroll
-        for (int p = kDigitRows - 1; p >= 1; --p) {
+        for (int p = D - 1; p >= 1; --p) {
             const int dg = (int)((r + 4) & 7) - 4;
             word[p] |= e2m1_digit(dg) << (4 * e);
             r = (r - dg) >> 3;
         }
-        word[0] |= e2m1_digit((int)r) << (4 * e);  // r in {-1, 0, 1}: |z| <= 2^30 = 8^10
+        word[0] |= e2m1_digit((int)r) << (4 * e);  // r in {-1, 0, 1}: |z| <= 8^(D-1)
     }
-    uint32_t* dst = image + chunk * (kDigitRows * kUnitWords) + w;
+    uint32_t* dst = image + chunk * (D * kUnitWords) + w;
 #pragma unroll
-    for (int p = 0; p < kDigitRows; ++p) dst[p * kUnitWords] = word[p];
+    for (int p = 0; p < D; ++p) dst[p * kUnitWords] = word[p];
 }
 
 // ---- main kernel ------------------------------------------------------------
 
 struct TcArgs {
-    const uint32_t* image;  // K-chunks x 11 x 32 digit words (k_u_digits_f4)
+    const uint32_t* image;  // K-chunks x D x 32 digit words (k_u_digits_f4)
     int nstages, range_stages, nranges, ntiles;
     int64_t m;
     const double* dsc;      // {S, 1/S, sum u~}
-    double* p1;             // nranges x m: S 2^-30 X_j over the range
+    double* p1;             // nranges x m: S 2^-kBits X_j over the range
     int* err;               // set to a nonzero code if a wait ran out
 };
 
+template <int D>
 __global__ void __launch_bounds__(kThreads, 1) k_rmv_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
+    using F = Fx<D>;
+    constexpr int kGBytes = F::kGBytes, kOffBar = F::kOffBar;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = sm_addr(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -307,8 +331,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rmv_tc(const __grid_constant__ 
                     const int x = 128 * (st0 + k);
                     tma_2d(sP + s * kStageBytes, &tmap, x, kTile * tile, pfull(s));
                     tma_2d(sP + s * kStageBytes + kBoxBytes, &tmap, x, kTile * tile + kBox, pfull(s));
-                    bulk_g2s(sG + s * kGBytes, a.image + (size_t)(st0 + k) * (2 * kDigitRows * kUnitWords), kGBytes,
-                             pfull(s));
+                    bulk_g2s(sG + s * kGBytes, a.image + (size_t)(st0 + k) * (2 * D * kUnitWords), kGBytes, pfull(s));
                 }
             }
             // drain: every issued copy has landed before the CTA may exit
@@ -353,8 +376,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_rmv_tc(const __grid_constant__ 
             }
         }
     } else if (warp == kWarpDigits) {
-        // ---- digits: rows 0-10 of each K-chunk, from the stage's shared-memory copy into
-        // tensor memory (lanes 0-31; rows 11-31 zero)
+        // ---- digits: the D rows of each K-chunk, from the stage's shared-memory copy into
+        // tensor memory (lane L holds digit row digit_of_lane(L); the other lanes zero)
+        const int prow = F::digit_of_lane(lane);
         uint32_t ps = 0, du = 0;
         bool ok = true;
         for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
@@ -370,9 +394,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_rmv_tc(const __grid_constant__ 
                 for (int h = 0; h < 2; ++h, ++du) {
                     const int ga = (int)(du % kRA);
                     uint32_t v[32];
-                    if (lane < kDigitRows) {
+                    if (prow >= 0) {
                         const uint4* src = reinterpret_cast<const uint4*>(sb + kOffG + s * kGBytes +
-                                                                          (h * kDigitRows + lane) * kUnitWords * 4);
+                                                                          (h * D + prow) * kUnitWords * 4);
 #pragma unroll
                         for (int c = 0; c < 8; ++c) {
                             const uint4 q = src[c];
@@ -402,10 +426,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_rmv_tc(const __grid_constant__ 
             }
         }
     } else if (warp == kWarpEpi) {
-        // ---- epilogue: lane p = digit row p; X_j = sum_p 8^(10-p) 2 F_p,j over lanes 0-15
+        // ---- epilogue: X_j = sum_p 8^(D-1-p) 2 F_p,j, summed per 16-lane half in 64-bit
+        // integers (X0 over the digits of lanes 0-15, X1 over those of lanes 16-31) and
+        // recombined as X0 8^(D-kHalf0) + X1
         uint32_t li = 0;
-        const double sc = ldexp(a.dsc[0], -30);
-        const int p = lane & 15, sh = 3 * (kDigitRows - 1 - lane);
+        const double sc = ldexp(a.dsc[0], -F::kBits);
+        const int p = lane & 15, dl = F::digit_of_lane(lane);
+        const int sh = dl < 0 ? 0 : (lane < 16 ? 3 * (F::kHalf0 - 1 - dl) : 3 * (D - 1 - dl));
         for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++li) {
             const int tile = item / a.nranges, range = item % a.nranges;
             if (!tc::bar_wait_warp(afull, li & 1u)) {
@@ -427,12 +454,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_rmv_tc(const __grid_constant__ 
                     long long v[16];
 #pragma unroll
                     for (int i = 0; i < 16; ++i)
-                        v[i] = lane < kDigitRows
-                                   ? (long long)__float2int_rn(2.f * __uint_as_float(r[16 * h + i])) << sh
-                                   : 0LL;
+                        v[i] = dl >= 0 ? (long long)__float2int_rn(2.f * __uint_as_float(r[16 * h + i])) << sh : 0LL;
                     bt_reduce_scatter<16>(v, p);
+                    double X = (double)v[0];
+                    if constexpr (D > F::kHalf0) {
+                        const long long x1 = shfl_xor_ll(v[0], 16);
+                        X = ldexp(X, 3 * (D - F::kHalf0)) + (double)x1;
+                    }
                     const int64_t j = (int64_t)tile * kTile + 32 * g + 16 * h + p;
-                    if (lane < 16 && j < a.m) a.p1[(int64_t)range * a.m + j] = sc * (double)v[0];
+                    if (lane < 16 && j < a.m) a.p1[(int64_t)range * a.m + j] = sc * X;
                 }
             }
         }
@@ -550,17 +580,19 @@ __global__ void __launch_bounds__(256) k_miss_fill(const uint8_t* __restrict__ p
     }
 }
 
-// Z_j = sum of z_i over the listed missing samples of SNP j, exact in 64-bit
-// integers, as p3[j] = S 2^-30 Z_j.  Eight lanes per SNP, four SNPs per warp,
+// Z_j = sum of z_i over the listed missing samples of SNP j, as p3[j] =
+// S 2^-bits Z_j.  z_i = 2^30 hi_i + lo_i (lo_i in [0, 2^30)): the two parts are
+// summed exactly in 64-bit integers (at most 2^32 entries of at most 2^27 and
+// 2^30) and joined once in FP64.  Eight lanes per SNP, four SNPs per warp,
 // eight list entries in flight per lane (the kernel is bound by the latency
 // of its loads times the number of warp waves; z is L2-resident).
 __global__ void __launch_bounds__(256) k_miss_sum(const int64_t* __restrict__ off, const uint32_t* __restrict__ idx,
-                                                   int64_t m, int64_t nz, const int* __restrict__ z,
+                                                   int64_t m, int64_t nz, const long long* __restrict__ z, int bits,
                                                    const double* __restrict__ dsc, double* __restrict__ p3,
                                                    int* __restrict__ err) {
     const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
     const int sl = threadIdx.x & 7;
-    long long zs = 0;
+    long long zh = 0, zl = 0;
     if (j < m) {
         const int64_t e1 = off[j + 1];
         for (int64_t e = off[j] + sl; e < e1; e += 64) {
@@ -570,29 +602,35 @@ __global__ void __launch_bounds__(256) k_miss_sum(const int64_t* __restrict__ of
 #pragma unroll
             for (int q = 0; q < 8; ++q)
                 if (ii[q] != 0xFFFFFFFFu) {
-                    if (ii[q] < nz)
-                        zs += __ldg(z + ii[q]);
-                    else
+                    if (ii[q] < nz) {
+                        const long long zi = __ldg(z + ii[q]);
+                        zh += zi >> 30;
+                        zl += zi & ((1LL << 30) - 1);
+                    } else
                         atomicCAS(err, 0, 51);  // a listed sample outside the z array: skipped, reported
                 }
         }
     }
 #pragma unroll
-    for (int o = 4; o > 0; o >>= 1) zs += __shfl_xor_sync(0xffffffffu, zs, o);
-    if (j < m && sl == 0) p3[j] = ldexp(dsc[0], -30) * (double)zs;
+    for (int o = 4; o > 0; o >>= 1) {
+        zh += __shfl_xor_sync(0xffffffffu, zh, o);
+        zl += __shfl_xor_sync(0xffffffffu, zl, o);
+    }
+    if (j < m && sl == 0) p3[j] = ldexp(dsc[0], -bits) * (ldexp((double)zh, 30) + (double)zl);
 }
 
 // ---- finishing kernel ----------------------------------------------------------
 
 // Sums over the K-ranges (fixed order), then
 //   x_j = d_j w_j [ (sum_r P1 - 3 sum_r P3) - mu_j (sum_i u~_i - sum_r P3) ]
-// (P1 = S 2^-30 sum c z over the range, missing codes counted as 3; P3 = the
+// (P1 = S 2^-bits sum c z over the range, missing codes counted as 3; P3 = the
 // missing samples' share), the subtraction of earlier basis vectors and the
 // solver's norm reduction.
+template <typename T>
 __global__ void __launch_bounds__(256) k_rmv_tc_fin(const double* __restrict__ p1, const double* __restrict__ p3,
                                                     int nr, int64_t m, const double* __restrict__ mu,
                                                     const double* __restrict__ d, const float* __restrict__ w,
-                                                    const double* __restrict__ dsc, float* __restrict__ x, FinArgs fa,
+                                                    const double* __restrict__ dsc, T* __restrict__ x, FinArgs fa,
                                                     Sv sv) {
     if (fa.role != ROLE_NONE && sv.sc->abort) return;
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -605,9 +643,9 @@ __global__ void __launch_bounds__(256) k_rmv_tc_fin(const double* __restrict__ p
         if (w) dw *= (double)w[j];
         const double obs_g = hsum - 3.0 * msum;  // sum of g u~ over the observed samples
         const double obs = dsc[2] - msum;        // sum of u~ over the observed samples
-        float val = (float)(dw * (obs_g - mu[j] * obs));
-        const float* W = static_cast<const float*>(fa.W);
-        for (int q = 0; q < fa.nsub; ++q) val -= (float)fa.bcol[q] * W[j + (int64_t)q * fa.ldw];
+        T val = (T)(dw * (obs_g - mu[j] * obs));
+        const T* W = static_cast<const T*>(fa.W);
+        for (int q = 0; q < fa.nsub; ++q) val -= (T)fa.bcol[q] * W[j + (int64_t)q * fa.ldw];
         x[j] = val;
         sq = (double)val * (double)val;
     }
@@ -674,8 +712,8 @@ static TcPlan plan_tc(const gkl_handle* h) {
     p.nranges = (p.nstages + p.range_stages - 1) / p.range_stages;
     p.grid = (int)std::min<int64_t>((int64_t)p.ntiles * p.nranges, sms);
     p.nwords = (int64_t)2 * p.nstages * kUnitWords;
-    p.img_bytes = (size_t)2 * p.nstages * kDigitRows * kUnitWords * sizeof(uint32_t);
-    p.z_bytes = (size_t)p.nstages * kStageSamples * sizeof(int);
+    p.img_bytes = (size_t)2 * p.nstages * Fx<kDigitsF64>::kGBytes / 2;  // the larger digit image
+    p.z_bytes = (size_t)p.nstages * kStageSamples * sizeof(long long);
     p.part_bytes = ((size_t)p.nranges + 1) * (size_t)h->m * sizeof(double);  // P1 per K-range, P3
     return p;
 }
@@ -711,7 +749,10 @@ bool tc_prepare(gkl_handle* h) {
     if (r != CUDA_SUCCESS) return false;
     static_assert(sizeof(CUtensorMap) == sizeof(h->tc_map), "tensor map size");
     memcpy(h->tc_map, &map, sizeof(map));
-    if (cudaFuncSetAttribute(k_rmv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_rmv_tc<kDigitsF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Fx<kDigitsF32>::kSmem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_rmv_tc<kDigitsF64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Fx<kDigitsF64>::kSmem) != cudaSuccess)
         return false;
     // list of missing codes per SNP (CSR), built once: counts, host prefix sum, fill
     const int64_t m = h->m;
@@ -742,12 +783,16 @@ bool tc_prepare(gkl_handle* h) {
     return true;
 }
 
-// Scale pass, digit image, the MMA kernel and the finishing kernel.
-cudaError_t launch_rmatvec_tc(const gkl_handle* h, const float* u, float* x, void* scratch, const Sv* sv,
-                              const FinArgs* fa, cudaEvent_t ev0, cudaEvent_t ev1, int* nlaunch) {
+// Scale pass, digit image, the MMA kernel, the missing codes' sum and the
+// finishing kernel; 11 digits for an FP32 product, 20 for an FP64 one.
+template <typename T>
+cudaError_t launch_rmatvec_tc(const gkl_handle* h, const T* u, T* x, void* scratch, const Sv* sv, const FinArgs* fa,
+                              cudaEvent_t ev0, cudaEvent_t ev1, int* nlaunch) {
+    constexpr int D = sizeof(T) == sizeof(float) ? kDigitsF32 : kDigitsF64;
+    if (h->tc_state <= 0) return cudaErrorNotSupported;
     const TcPlan p = plan_tc(h);
     uint32_t* img = static_cast<uint32_t*>(scratch);
-    int* z = reinterpret_cast<int*>(reinterpret_cast<char*>(scratch) + al256(p.img_bytes));
+    long long* z = reinterpret_cast<long long*>(reinterpret_cast<char*>(scratch) + al256(p.img_bytes));
     double* p1 = reinterpret_cast<double*>(reinterpret_cast<char*>(z) + al256(p.z_bytes));
     double* p3 = p1 + (size_t)p.nranges * h->m;
     double* aux = h->aux;  // dsc[4] | counter | partials of the scale pass; error word at kAuxErrOffset
@@ -758,29 +803,35 @@ cudaError_t launch_rmatvec_tc(const gkl_handle* h, const float* u, float* x, voi
     cudaStream_t st = h->stream;
     const int sblocks = std::min(2 * h->num_sms, (int)((h->n + 255) / 256));
     GKL_DEBUG_SYNC(st, "before A^T u");
-    k_u_scale<<<std::max(1, sblocks), 256, 0, st>>>(u, h->s, h->n, part, counter, dsc);
+    k_u_scale<T><<<std::max(1, sblocks), 256, 0, st>>>(u, h->s, h->n, part, counter, dsc);
     GKL_DEBUG_SYNC(st, "k_u_scale");
-    k_u_digits_f4<<<(unsigned)((p.nwords + 255) / 256), 256, 0, st>>>(u, h->s, h->n, p.nwords, dsc, img, z);
+    k_u_digits_f4<T, D><<<(unsigned)((p.nwords + 255) / 256), 256, 0, st>>>(u, h->s, h->n, p.nwords, dsc, img, z);
     GKL_DEBUG_SYNC(st, "k_u_digits_f4");
     alignas(64) CUtensorMap map;
     memcpy(&map, h->tc_map, sizeof(map));
     TcArgs a{img, p.nstages, p.range_stages, p.nranges, p.ntiles, h->m, dsc, p1, err};
     if (ev0) cudaEventRecord(ev0, st);
-    k_rmv_tc<<<p.grid, kThreads, kSmemBytes, st>>>(map, a);
+    k_rmv_tc<D><<<p.grid, kThreads, Fx<D>::kSmem, st>>>(map, a);
     if (ev1) cudaEventRecord(ev1, st);
     GKL_DEBUG_SYNC(st, "k_rmv_tc");
     k_miss_sum<<<(unsigned)((h->m * 8 + 255) / 256), 256, 0, st>>>(h->miss_off, h->miss_idx, h->m,
-                                                                    (int64_t)p.nstages * kStageSamples, z, dsc, p3, err);
+                                                                    (int64_t)p.nstages * kStageSamples, z,
+                                                                    Fx<D>::kBits, dsc, p3, err);
     GKL_DEBUG_SYNC(st, "k_miss_sum");
     FinArgs f{};
     Sv s{};
     if (fa) f = *fa;
     if (sv) s = *sv;
-    k_rmv_tc_fin<<<(unsigned)((h->m + 255) / 256), 256, 0, st>>>(p1, p3, p.nranges, h->m, h->mu, h->d, h->w, dsc, x,
-                                                                  f, s);
+    k_rmv_tc_fin<T><<<(unsigned)((h->m + 255) / 256), 256, 0, st>>>(p1, p3, p.nranges, h->m, h->mu, h->d, h->w, dsc,
+                                                                     x, f, s);
     GKL_DEBUG_SYNC(st, "k_rmv_tc_fin");
     if (nlaunch) *nlaunch = 5;
     return cudaGetLastError();
 }
+
+template cudaError_t launch_rmatvec_tc<float>(const gkl_handle*, const float*, float*, void*, const Sv*,
+                                              const FinArgs*, cudaEvent_t, cudaEvent_t, int*);
+template cudaError_t launch_rmatvec_tc<double>(const gkl_handle*, const double*, double*, void*, const Sv*,
+                                               const FinArgs*, cudaEvent_t, cudaEvent_t, int*);
 
 }  // namespace gkl
