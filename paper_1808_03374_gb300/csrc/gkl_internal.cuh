@@ -121,9 +121,9 @@ struct gkl_handle {
     alignas(64) unsigned char tc_map[128];  // TMA descriptor of the packed matrix (A^T u: 128 B x 128 rows, swizzled)
     alignas(64) unsigned char mv_map[128];  // TMA descriptor for A v (256 B x 32 rows, no swizzle)
     int* mv_err;     // error word of the A v kernel when the handle has no aux buffer (allocation-free product)
-    int64_t* miss_off;   // list of the missing codes per SNP (m + 1 offsets), built by tc_prepare
-    uint32_t* miss_idx;  // their sample indices, ascending per SNP
-    int64_t miss_nnz;
+    int64_t* miss_off;   // list of the missing codes per (sample block, SNP): nb m + 1 offsets, built by tc_prepare
+    uint16_t* miss_idx;  // their offsets in the sample block, ascending, padded to multiples of 8
+    int64_t miss_nnz;    // entries of the list, padding included
     char err[512];
 };
 
@@ -180,7 +180,7 @@ enum MemKind { MEM_BAD = 0, MEM_DEVICE = 1, MEM_HOST = 2 };
 int mem_kind(const void* p, int device);
 // S = U diag(sigma) (n x k, column-major) in the type of prec (GKL_FP64: double, else float)
 cudaError_t launch_scores(cudaStream_t st, int prec, const void* U, const double* sigma, int64_t n, int k, void* S);
-// tcgen05 A^T u (FP32 path, packed_tc.cu); tc_prepare builds the TMA descriptor and the
+// tcgen05 A^T u (both precisions, packed_tc.cu); tc_prepare builds the TMA descriptor and the
 // list of missing codes once per handle.
 bool tc_prepare(gkl_handle* h);
 size_t rmv_tc_scratch_bytes(const gkl_handle* h);

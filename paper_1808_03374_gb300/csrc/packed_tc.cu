@@ -50,6 +50,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "epilogue.cuh"
@@ -94,6 +95,7 @@ template <int D>
 struct Fx {
     static constexpr int kBits = 3 * (D - 1);
     static constexpr int kHalf0 = D <= 11 ? D : D / 2;
+    using Z = std::conditional_t<(D <= 11), int, long long>;  // holds z_i (|z_i| <= 2^kBits)
     static constexpr int kGBytes = 2 * D * kUnitWords * 4;  // digit rows of one stage (2 K-chunks)
     static constexpr int kOffBar = kOffG + kRP * kGBytes;
     static constexpr int kSmem = 1024 + kOffBar + 1024;
@@ -206,7 +208,8 @@ __device__ __forceinline__ uint32_t e2m1_digit(int dg) {
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_u_digits_f4(const T* __restrict__ u, const float* __restrict__ s, int64_t n,
                                                       int64_t nwords, const double* __restrict__ dsc,
-                                                      uint32_t* __restrict__ image, long long* __restrict__ zout) {
+                                                      uint32_t* __restrict__ image,
+                                                      typename Fx<D>::Z* __restrict__ zout) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nwords) return;
     const int64_t chunk = t / kUnitWords;
@@ -225,7 +228,7 @@ __global__ void __launch_bounds__(256) k_u_digits_f4(const T* __restrict__ u, co
             const double x = (double)u[i] * (s ? (double)s[i] : 1.0) * inv;  // |x| < 1
             z = __double2ll_rn(ldexp(x, Fx<D>::kBits));
         }
-        zout[i] = z;
+        zout[i] = (typename Fx<D>::Z)z;
         long long r = z;
 #pragma unroll
         for (int p = D - 1; p >= 1; --p) {
@@ -526,97 +529,179 @@ __global__ void __launch_bounds__(kThreads, 1) k_rmv_tc(const __grid_constant__ 
 }
 
 // ---- the list of missing codes and its per-product sum ------------------------
+//
+// The samples are cut into blocks of kMissBlock; segment (b, j) lists the
+// missing samples of SNP j in block b as 16-bit offsets into the block,
+// ascending, padded with kMissPad to a multiple of 8 entries (one 16-byte
+// load).  Segments are stored block-major, off[b m + j] is the first entry of
+// segment (b, j) and off[nb m] the list's length.  Per product one CTA holds
+// the z values of one block in shared memory and gathers them there for a
+// chunk of SNPs: the list is read once from HBM (2 bytes an entry) and the
+// gathers never leave the SM.
 
-// counts[j] = missing codes of SNP j among samples 0..n-1; one warp per SNP.
-__global__ void __launch_bounds__(256) k_miss_count(const uint8_t* __restrict__ packed, int64_t stride, int64_t n,
-                                                     int64_t m, int* __restrict__ counts) {
-    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (j >= m) return;
-    const uint32_t* row = reinterpret_cast<const uint32_t*>(packed + j * stride);
-    const int64_t words = (n + 15) / 16;
-    int c = 0;
-    for (int64_t wd = lane; wd < words; wd += 32) {
-        uint32_t Y = row[wd] & (row[wd] >> 1) & 0x55555555u;
-        const int64_t valid = n - wd * 16;  // samples of this word below n
-        if (valid < 16) Y &= (1u << (2 * valid)) - 1u;
-        c += __popc(Y);
-    }
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (lane == 0) counts[j] = c;
+constexpr int kMissBlock = 24576;       // samples a block: its int64 z values fill 192 KB of shared memory
+constexpr uint16_t kMissPad = 0xFFFFu;  // padding entry (above every offset in a block)
+constexpr int kMissThreads = 1024;
+static_assert(kMissBlock % 16 == 0 && kMissBlock < kMissPad, "block of the missing-code list");
+
+// Missing-code mask of packed word wd of a row (bit 2 s set where sample 16 wd + s has code 3),
+// samples at or above n cleared.
+__device__ __forceinline__ uint32_t miss_mask(const uint32_t* row, int64_t wd, int64_t n) {
+    uint32_t Y = row[wd] & (row[wd] >> 1) & 0x55555555u;
+    const int64_t valid = n - wd * 16;
+    if (valid < 16) Y &= (1u << (2 * valid)) - 1u;
+    return Y;
 }
 
-// idx[off[j] ..] = the missing sample indices of SNP j, ascending; one warp per SNP.
-__global__ void __launch_bounds__(256) k_miss_fill(const uint8_t* __restrict__ packed, int64_t stride, int64_t n,
-                                                    int64_t m, const int64_t* __restrict__ off,
-                                                    uint32_t* __restrict__ idx) {
-    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// counts[b m + j] = missing codes of SNP j in sample block b; one warp per (j, b).
+__global__ void __launch_bounds__(256) k_miss_count(const uint8_t* __restrict__ packed, int64_t stride, int64_t n,
+                                                     int64_t m, int nb, int* __restrict__ counts) {
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (j >= m) return;
+    if (gw >= m * nb) return;
+    const int64_t j = gw / nb;
+    const int b = (int)(gw % nb);
     const uint32_t* row = reinterpret_cast<const uint32_t*>(packed + j * stride);
     const int64_t words = (n + 15) / 16;
-    int64_t pos = off[j];
-    for (int64_t w0 = 0; w0 < words; w0 += 32) {
-        const int64_t wd = w0 + lane;
-        uint32_t Y = 0;
-        if (wd < words) {
-            Y = row[wd] & (row[wd] >> 1) & 0x55555555u;
-            const int64_t valid = n - wd * 16;
-            if (valid < 16) Y &= (1u << (2 * valid)) - 1u;
-        }
+    const int64_t w0 = (int64_t)b * (kMissBlock / 16), w1 = min(words, w0 + kMissBlock / 16);
+    int c = 0;
+    for (int64_t wd = w0 + lane; wd < w1; wd += 32) c += __popc(miss_mask(row, wd, n));
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) counts[(int64_t)b * m + j] = c;
+}
+
+// Writes segment (b, j) of the list and its padding; one warp per (j, b).
+__global__ void __launch_bounds__(256) k_miss_fill(const uint8_t* __restrict__ packed, int64_t stride, int64_t n,
+                                                    int64_t m, int nb, const int64_t* __restrict__ off,
+                                                    uint16_t* __restrict__ idx) {
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= m * nb) return;
+    const int64_t j = gw / nb;
+    const int b = (int)(gw % nb);
+    const uint32_t* row = reinterpret_cast<const uint32_t*>(packed + j * stride);
+    const int64_t words = (n + 15) / 16;
+    const int64_t w0 = (int64_t)b * (kMissBlock / 16), w1 = min(words, w0 + kMissBlock / 16);
+    const int64_t seg = (int64_t)b * m + j;
+    int64_t pos = off[seg];
+    const int64_t end = off[seg + 1];
+    for (int64_t wb = w0; wb < w1; wb += 32) {
+        const int64_t wd = wb + lane;
+        uint32_t Y = wd < w1 ? miss_mask(row, wd, n) : 0u;
         const int c = __popc(Y);
         int incl = c;
         for (int o = 1; o < 32; o <<= 1) {
             const int v = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += v;
         }
-        int64_t p = pos + incl - c;
+        int64_t q = pos + incl - c;
         while (Y) {
             const int bit = __ffs(Y) - 1;
             Y &= Y - 1u;
-            idx[p++] = (uint32_t)(wd * 16 + (bit >> 1));
+            if (q < end) idx[q] = (uint16_t)((wd - w0) * 16 + (bit >> 1));
+            ++q;
         }
         pos += __shfl_sync(0xffffffffu, incl, 31);
     }
+    for (int64_t q = pos + lane; q < end; q += 32) idx[q] = kMissPad;
 }
 
-// Z_j = sum of z_i over the listed missing samples of SNP j, as p3[j] =
-// S 2^-bits Z_j.  z_i = 2^30 hi_i + lo_i (lo_i in [0, 2^30)): the two parts are
-// summed exactly in 64-bit integers (at most 2^32 entries of at most 2^27 and
-// 2^30) and joined once in FP64.  Eight lanes per SNP, four SNPs per warp,
-// eight list entries in flight per lane (the kernel is bound by the latency
-// of its loads times the number of warp waves; z is L2-resident).
-__global__ void __launch_bounds__(256) k_miss_sum(const int64_t* __restrict__ off, const uint32_t* __restrict__ idx,
-                                                   int64_t m, int64_t nz, const long long* __restrict__ z, int bits,
-                                                   const double* __restrict__ dsc, double* __restrict__ p3,
-                                                   int* __restrict__ err) {
-    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
-    const int sl = threadIdx.x & 7;
-    long long zh = 0, zl = 0;
-    if (j < m) {
-        const int64_t e1 = off[j + 1];
-        for (int64_t e = off[j] + sl; e < e1; e += 64) {
-            uint32_t ii[8];
+// p3[b m + j] = S 2^-bits Z_bj, Z_bj = sum of z_i over the missing samples of
+// SNP j in block b.  The sum is exact: 64-bit integers (ZT = int), or for
+// 64-bit z the parts z = 2^30 hi + lo (lo in [0, 2^30)) summed apart and
+// joined once in FP64.  Persistent: CTA c takes the segments [s0, s1) of the
+// block-major order (one contiguous run of the list), loads the z values of
+// each block its run touches into shared memory, and walks the run in batches
+// of 128 segments, eight lanes a segment; the first 256 entries of a segment
+// come in four 16-byte loads a lane, issued one batch ahead (the offsets two
+// batches ahead) so that the loads overlap the gathers of the batch before.
+struct MissSeg {
+    int64_t e0, e1;  // 16-byte units of the list
+};
+
+__device__ __forceinline__ MissSeg miss_seg(const int64_t* __restrict__ off, int64_t s, int64_t a1) {
+    if (s >= a1) return MissSeg{0, 0};
+    return MissSeg{__ldcs(off + s) >> 3, __ldcs(off + s + 1) >> 3};
+}
+
+__device__ __forceinline__ void miss_load(const uint4* __restrict__ src, MissSeg g, int sl, uint4 (&q)[4]) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) ii[q] = e + 8 * q < e1 ? __ldg(idx + e + 8 * q) : 0xFFFFFFFFu;
+    for (int r = 0; r < 4; ++r) {
+        const int64_t e = g.e0 + sl + 8 * r;
+        q[r] = e < g.e1 ? __ldcs(src + e) : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+    }
+}
+
+template <typename ZT>
+__device__ __forceinline__ void miss_gather(const uint4 q, const ZT* zs, int cnt, long long& zh, long long& zl,
+                                            bool& bad) {
+    const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                if (ii[q] != 0xFFFFFFFFu) {
-                    if (ii[q] < nz) {
-                        const long long zi = __ldg(z + ii[q]);
-                        zh += zi >> 30;
-                        zl += zi & ((1LL << 30) - 1);
-                    } else
-                        atomicCAS(err, 0, 51);  // a listed sample outside the z array: skipped, reported
-                }
+    for (int c = 0; c < 8; ++c) {
+        const uint32_t o = (wv[c >> 1] >> (16 * (c & 1))) & 0xFFFFu;
+        if (o < (uint32_t)cnt) {
+            const long long zi = (long long)zs[o];
+            if constexpr (sizeof(ZT) == 4) {
+                zl += zi;
+            } else {
+                zh += zi >> 30;
+                zl += zi & ((1LL << 30) - 1);
+            }
+        } else if (o != kMissPad) {
+            bad = true;
         }
     }
+}
+
+template <typename ZT>
+__global__ void __launch_bounds__(kMissThreads, 1) k_miss_sum(const int64_t* __restrict__ off,
+                                                               const uint16_t* __restrict__ idx, int64_t m, int nb,
+                                                               const ZT* __restrict__ z, int64_t zlen, int bits,
+                                                               const double* __restrict__ dsc, double* __restrict__ p3,
+                                                               int* __restrict__ err) {
+    extern __shared__ __align__(16) uint8_t miss_smem[];
+    ZT* zs = reinterpret_cast<ZT*>(miss_smem);
+    constexpr int kGroups = kMissThreads / 8;
+    const int grp = threadIdx.x >> 3, sl = threadIdx.x & 7;
+    const int64_t nseg = m * nb;
+    const int64_t per = (nseg + gridDim.x - 1) / gridDim.x;
+    const int64_t s0 = (int64_t)blockIdx.x * per, s1 = min(nseg, s0 + per);
+    const double sc = ldexp(dsc[0], -bits);
+    const uint4* src = reinterpret_cast<const uint4*>(idx);
+    bool bad = false;
+    for (int64_t b = s0 / m; s0 < s1 && b * m < s1; ++b) {
+        const int64_t a0 = max(s0, b * m), a1 = min(s1, (b + 1) * m);
+        const int64_t z0 = b * kMissBlock;
+        const int cnt = (int)min((int64_t)kMissBlock, zlen - z0);
+        __syncthreads();  // the previous block's gathers are done
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) zs[i] = z[z0 + i];
+        __syncthreads();
+        MissSeg cur = miss_seg(off, a0 + grp, a1);
+        MissSeg nxt = miss_seg(off, a0 + kGroups + grp, a1);
+        uint4 q[4], qn[4];
+        miss_load(src, cur, sl, q);
+        for (int64_t sb = a0; sb < a1; sb += kGroups) {  // the same trip count in every lane
+            const int64_t s = sb + grp;
+            miss_load(src, nxt, sl, qn);                                  // batch t + 1
+            const MissSeg nn = miss_seg(off, sb + 2 * kGroups + grp, a1);  // batch t + 2
+            long long zh = 0, zl = 0;
 #pragma unroll
-    for (int o = 4; o > 0; o >>= 1) {
-        zh += __shfl_xor_sync(0xffffffffu, zh, o);
-        zl += __shfl_xor_sync(0xffffffffu, zl, o);
+            for (int r = 0; r < 4; ++r) miss_gather<ZT>(q[r], zs, cnt, zh, zl, bad);
+            for (int64_t e = cur.e0 + 32 + sl; e < cur.e1; e += 8)  // entries beyond the first 256
+                miss_gather<ZT>(__ldcs(src + e), zs, cnt, zh, zl, bad);
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) {
+                zh += __shfl_xor_sync(0xffffffffu, zh, o);
+                zl += __shfl_xor_sync(0xffffffffu, zl, o);
+            }
+            if (s < a1 && sl == 0) p3[s] = sc * (ldexp((double)zh, 30) + (double)zl);
+            cur = nxt;
+            nxt = nn;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) q[r] = qn[r];
+        }
     }
-    if (j < m && sl == 0) p3[j] = ldexp(dsc[0], -bits) * (ldexp((double)zh, 30) + (double)zl);
+    if (bad) atomicCAS(err, 0, 51);  // an offset outside its block: skipped, reported
 }
 
 // ---- finishing kernel ----------------------------------------------------------
@@ -628,7 +713,7 @@ __global__ void __launch_bounds__(256) k_miss_sum(const int64_t* __restrict__ of
 // solver's norm reduction.
 template <typename T>
 __global__ void __launch_bounds__(256) k_rmv_tc_fin(const double* __restrict__ p1, const double* __restrict__ p3,
-                                                    int nr, int64_t m, const double* __restrict__ mu,
+                                                    int nr, int nb, int64_t m, const double* __restrict__ mu,
                                                     const double* __restrict__ d, const float* __restrict__ w,
                                                     const double* __restrict__ dsc, T* __restrict__ x, FinArgs fa,
                                                     Sv sv) {
@@ -638,7 +723,7 @@ __global__ void __launch_bounds__(256) k_rmv_tc_fin(const double* __restrict__ p
     if (j < m) {
         double hsum = 0.0, msum = 0.0;
         for (int r = 0; r < nr; ++r) hsum += p1[(int64_t)r * m + j];
-        msum = p3[j];
+        for (int b = 0; b < nb; ++b) msum += p3[(int64_t)b * m + j];
         double dw = d[j];
         if (w) dw *= (double)w[j];
         const double obs_g = hsum - 3.0 * msum;  // sum of g u~ over the observed samples
@@ -685,6 +770,7 @@ static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct TcPlan {
     int nstages, range_stages, nranges, ntiles, grid;
+    int nb, miss_grid;  // sample blocks of the missing-code list; CTAs of its sum
     int64_t nwords;  // digit-image words of one row: K-chunks x 32
     size_t img_bytes, z_bytes, part_bytes;
 };
@@ -714,7 +800,9 @@ static TcPlan plan_tc(const gkl_handle* h) {
     p.nwords = (int64_t)2 * p.nstages * kUnitWords;
     p.img_bytes = (size_t)2 * p.nstages * Fx<kDigitsF64>::kGBytes / 2;  // the larger digit image
     p.z_bytes = (size_t)p.nstages * kStageSamples * sizeof(long long);
-    p.part_bytes = ((size_t)p.nranges + 1) * (size_t)h->m * sizeof(double);  // P1 per K-range, P3
+    p.nb = (int)std::max<int64_t>(1, (h->n + kMissBlock - 1) / kMissBlock);
+    p.miss_grid = (int)std::max<int64_t>(1, std::min<int64_t>(sms, (h->m * p.nb + 127) / 128));
+    p.part_bytes = ((size_t)p.nranges + p.nb) * (size_t)h->m * sizeof(double);  // P1 per K-range, P3 per block
     return p;
 }
 
@@ -725,9 +813,9 @@ size_t rmv_tc_scratch_bytes(const gkl_handle* h) {
 
 // Prepares the tensor-core path for a handle: the TMA descriptor of the packed
 // matrix (128-byte x 128-row boxes, 128-byte swizzle) and the kernel's
-// shared-memory limit, and the list of missing codes per SNP.  Returns false (gkl_init then fails: the FP32 A^T u has
-// no other kernel) if the driver entry point or a step is unavailable or the
-// packed buffer is not 16-byte aligned.
+// shared-memory limits, and the list of missing codes.  Returns false
+// (gkl_init then fails: A^T u has no other kernel) if the driver entry point
+// or a step is unavailable or the packed buffer is not 16-byte aligned.
 bool tc_prepare(gkl_handle* h) {
     if (h->tc_state != 0) return h->tc_state > 0;
     h->tc_state = -1;
@@ -754,29 +842,38 @@ bool tc_prepare(gkl_handle* h) {
         cudaFuncSetAttribute(k_rmv_tc<kDigitsF64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              Fx<kDigitsF64>::kSmem) != cudaSuccess)
         return false;
-    // list of missing codes per SNP (CSR), built once: counts, host prefix sum, fill
+    if (cudaFuncSetAttribute(k_miss_sum<int>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kMissBlock * (int)sizeof(int)) != cudaSuccess ||
+        cudaFuncSetAttribute(k_miss_sum<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kMissBlock * (int)sizeof(long long)) != cudaSuccess)
+        return false;
+    // list of missing codes per (sample block, SNP), built once: counts, host prefix sum of the
+    // padded counts, fill
     const int64_t m = h->m;
+    const int64_t nb64 = std::max<int64_t>(1, (h->n + kMissBlock - 1) / kMissBlock);
+    const int nb = (int)nb64;
+    const int64_t nseg = m * nb;
     int* counts = nullptr;
-    std::vector<int> hc((size_t)m);
-    std::vector<int64_t> ho((size_t)m + 1);
-    const unsigned wblocks = (unsigned)((m * 32 + 255) / 256);
-    cudaError_t e = cudaMalloc(&counts, sizeof(int) * m);
+    std::vector<int> hc((size_t)nseg);
+    std::vector<int64_t> ho((size_t)nseg + 1);
+    const unsigned wblocks = (unsigned)((nseg * 32 + 255) / 256);
+    cudaError_t e = cudaMalloc(&counts, sizeof(int) * nseg);
     if (e == cudaSuccess) {
-        k_miss_count<<<wblocks, 256, 0, h->stream>>>(h->packed, h->stride, h->n, m, counts);
-        e = cudaMemcpyAsync(hc.data(), counts, sizeof(int) * m, cudaMemcpyDeviceToHost, h->stream);
+        k_miss_count<<<wblocks, 256, 0, h->stream>>>(h->packed, h->stride, h->n, m, nb, counts);
+        e = cudaMemcpyAsync(hc.data(), counts, sizeof(int) * nseg, cudaMemcpyDeviceToHost, h->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (counts) cudaFree(counts);
     if (e != cudaSuccess) return false;
     ho[0] = 0;
-    for (int64_t j = 0; j < m; ++j) ho[j + 1] = ho[j] + hc[j];
-    h->miss_nnz = ho[m];
-    e = cudaMalloc(&h->miss_off, sizeof(int64_t) * (m + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&h->miss_idx, sizeof(uint32_t) * std::max<int64_t>(1, h->miss_nnz));
+    for (int64_t q = 0; q < nseg; ++q) ho[q + 1] = ho[q] + ((hc[q] + 7) & ~7);
+    h->miss_nnz = ho[nseg];
+    e = cudaMalloc(&h->miss_off, sizeof(int64_t) * (nseg + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&h->miss_idx, sizeof(uint16_t) * std::max<int64_t>(8, h->miss_nnz));
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->miss_off, ho.data(), sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, h->stream);
+        e = cudaMemcpyAsync(h->miss_off, ho.data(), sizeof(int64_t) * (nseg + 1), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
-        k_miss_fill<<<wblocks, 256, 0, h->stream>>>(h->packed, h->stride, h->n, m, h->miss_off, h->miss_idx);
+        k_miss_fill<<<wblocks, 256, 0, h->stream>>>(h->packed, h->stride, h->n, m, nb, h->miss_off, h->miss_idx);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return false;
     h->tc_state = 1;
@@ -792,7 +889,8 @@ cudaError_t launch_rmatvec_tc(const gkl_handle* h, const T* u, T* x, void* scrat
     if (h->tc_state <= 0) return cudaErrorNotSupported;
     const TcPlan p = plan_tc(h);
     uint32_t* img = static_cast<uint32_t*>(scratch);
-    long long* z = reinterpret_cast<long long*>(reinterpret_cast<char*>(scratch) + al256(p.img_bytes));
+    using ZT = typename Fx<D>::Z;
+    ZT* z = reinterpret_cast<ZT*>(reinterpret_cast<char*>(scratch) + al256(p.img_bytes));
     double* p1 = reinterpret_cast<double*>(reinterpret_cast<char*>(z) + al256(p.z_bytes));
     double* p3 = p1 + (size_t)p.nranges * h->m;
     double* aux = h->aux;  // dsc[4] | counter | partials of the scale pass; error word at kAuxErrOffset
@@ -814,16 +912,15 @@ cudaError_t launch_rmatvec_tc(const gkl_handle* h, const T* u, T* x, void* scrat
     k_rmv_tc<D><<<p.grid, kThreads, Fx<D>::kSmem, st>>>(map, a);
     if (ev1) cudaEventRecord(ev1, st);
     GKL_DEBUG_SYNC(st, "k_rmv_tc");
-    k_miss_sum<<<(unsigned)((h->m * 8 + 255) / 256), 256, 0, st>>>(h->miss_off, h->miss_idx, h->m,
-                                                                    (int64_t)p.nstages * kStageSamples, z,
-                                                                    Fx<D>::kBits, dsc, p3, err);
+    k_miss_sum<ZT><<<(unsigned)p.miss_grid, kMissThreads, kMissBlock * sizeof(ZT), st>>>(
+        h->miss_off, h->miss_idx, h->m, p.nb, z, (int64_t)p.nstages * kStageSamples, Fx<D>::kBits, dsc, p3, err);
     GKL_DEBUG_SYNC(st, "k_miss_sum");
     FinArgs f{};
     Sv s{};
     if (fa) f = *fa;
     if (sv) s = *sv;
-    k_rmv_tc_fin<T><<<(unsigned)((h->m + 255) / 256), 256, 0, st>>>(p1, p3, p.nranges, h->m, h->mu, h->d, h->w, dsc,
-                                                                     x, f, s);
+    k_rmv_tc_fin<T><<<(unsigned)((h->m + 255) / 256), 256, 0, st>>>(p1, p3, p.nranges, p.nb, h->m, h->mu, h->d, h->w,
+                                                                     dsc, x, f, s);
     GKL_DEBUG_SYNC(st, "k_rmv_tc_fin");
     if (nlaunch) *nlaunch = 5;
     return cudaGetLastError();
