@@ -124,6 +124,9 @@ typedef struct gkl_info {
     double ms_cgs;         /* profile != 0: summed duration of the reorthogonalisation kernels */
     int32_t second_u;      /* u reorthogonalisations that took a second Gram-Schmidt pass */
     int32_t second_v;      /* v reorthogonalisations that took a second pass (block forms: orthonormalisations) */
+    int32_t refine_cycles; /* block forms: times the true residual after the Rayleigh-Ritz step missed tol and the
+                              cycles went on with full-precision products (and a tighter estimate target) */
+    int32_t reserved1;
 } gkl_info;
 
 /* Fill *o with defaults: k=10, ell=30, k_keep=0, DGKS (the adaptive second

@@ -639,8 +639,86 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
     }
     if (e == cudaSuccess) e = orthonormalize(c, V, ldv, b, nullptr, ldv, 0, m, R);
     if (e != cudaSuccess) return fail("block start");
+    // output: U P[:, :k], V Q[:, :k]; for k <= 32 refined by one Rayleigh-Ritz
+    // step on span(V Q[:, :k]) with FP32-grade products (W = A V_k, W^T W = Y
+    // Lambda Y^T in FP64, sigma = sqrt(lambda), V = V_k Y, U = W Y / sigma),
+    // whose singular values are accurate to the square of the subspace angle,
+    // and the true residuals ||A^T u_i - sigma_i v_i|| from one more product
+    float* Uo = reinterpret_cast<float*>(W + oOutU);
+    float* Vo = reinterpret_cast<float*>(W + oOutV);
+    bool true_resid = false;  // maxrel holds the true residual (else the Lanczos estimate)
+    auto finalize = [&]() -> cudaError_t {
+    const int digits_iter = c.tc_digits;
+    c.tc_digits = 8;  // the Rayleigh-Ritz step and the residuals at full precision
+    cudaError_t e = cudaSuccess;
+    true_resid = false;
+    if (k <= kMaxB) {
+        float* Vk = V2;  // m x k (ldv)
+        float* Wk = U2;  // n x k (ldu)
+        std::vector<double> G, lam, Y, Rk;
+        e = launch_rotate<float>(c.st, V, ldv, ell, sv.Q, ell, k, Vk, ldv, m);
+        if (e == cudaSuccess) e = orthonormalize(c, Vk, ldv, k, nullptr, ldv, 0, m, Rk);
+        if (e == cudaSuccess) e = block_product(c, false, Vk, ldv, Wk, ldu, k);
+        if (e == cudaSuccess) e = gram(c, Wk, ldu, k, Wk, ldu, k, n, c.d_small);
+        if (e == cudaSuccess) e = download(c, c.d_small, G, (size_t)k * k);
+        if (e != cudaSuccess) return e;
+        sym_eig(k, G, lam, Y);
+        std::vector<int> ord(k);
+        for (int i = 0; i < k; ++i) ord[i] = i;
+        std::sort(ord.begin(), ord.end(), [&](int a, int b2) { return lam[a] > lam[b2]; });
+        std::vector<double> Cv((size_t)k * k), Cu((size_t)k * k), Cs((size_t)k * k, 0.0);
+        for (int j = 0; j < k; ++j) {
+            const double sj = std::sqrt(std::max(0.0, lam[ord[j]]));
+            sg[j] = sj;
+            for (int r = 0; r < k; ++r) {
+                Cv[r + (size_t)k * j] = Y[r + (size_t)k * ord[j]];
+                Cu[r + (size_t)k * j] = sj > 0.0 ? Y[r + (size_t)k * ord[j]] / sj : 0.0;
+            }
+            Cs[j + (size_t)k * j] = sj;
+        }
+        e = upload(c, Cv, c.d_small);
+        if (e == cudaSuccess) {
+            k_block_axpy<<<axpy_grid(c, m), 256, 0, c.st>>>(Vo, m, k, Vk, ldv, k, c.d_small, k, 0.f, 1.f, m);
+            e = cudaStreamSynchronize(c.st);  // d_small is reused below
+        }
+        if (e == cudaSuccess) e = upload(c, Cu, c.d_small);
+        if (e == cudaSuccess) {
+            k_block_axpy<<<axpy_grid(c, n), 256, 0, c.st>>>(Uo, n, k, Wk, ldu, k, c.d_small, k, 0.f, 1.f, n);
+            e = cudaStreamSynchronize(c.st);
+        }
+        // true residuals: Z = A^T U - V diag(sigma), r_i = ||Z_i||
+        if (e == cudaSuccess) e = block_product(c, true, Uo, n, Vk, ldv, k);
+        if (e == cudaSuccess) e = upload(c, Cs, c.d_small);
+        if (e == cudaSuccess) {
+            k_block_axpy<<<axpy_grid(c, m), 256, 0, c.st>>>(Vk, ldv, k, Vo, m, k, c.d_small, k, 1.f, -1.f, m);
+            e = cudaStreamSynchronize(c.st);
+        }
+        if (e == cudaSuccess) e = gram(c, Vk, ldv, k, Vk, ldv, k, m, c.d_small);
+        if (e == cudaSuccess) e = download(c, c.d_small, G, (size_t)k * k);
+        if (e != cudaSuccess) return e;
+        c.launches += 3;
+        double mxr = 0.0, sumr = 0.0;
+        for (int i = 0; i < k; ++i) {
+            res[i] = std::sqrt(std::max(0.0, G[i + (size_t)k * i]));
+            mxr = std::max(mxr, res[i]);
+            sumr += res[i];
+        }
+        maxrel = sg[0] > 0.0 ? mxr / sg[0] : 0.0;
+        dtheta = sumr;
+        true_resid = true;
+    } else {
+        e = launch_rotate<float>(c.st, U, ldu, ell, sv.P, ell, k, Uo, n, n);
+        if (e == cudaSuccess) e = launch_rotate<float>(c.st, V, ldv, ell, sv.Q, ell, k, Vo, m, m);
+    }
+    c.tc_digits = digits_iter;
+    return e;
+    };
+    double est_tol = o->tol;  // target of the Lanczos estimate; halved when the true residual misses tol
+    int refines = 0;
+    bool fresh = false;  // this cycle starts from a single start block (cycle 0, explicit restart)
     for (cycle = 0; cycle < o->maxit; ++cycle) {
-        const int c0 = cycle == 0 ? 0 : kk;
+        const int c0 = cycle == 0 || fresh ? 0 : kk;
+        fresh = false;
         for (int j0 = c0; j0 < ell; j0 += b) {
             float* Wb = U + (int64_t)j0 * ldu;
             cudaEventRecord(ev1, c.st);
@@ -713,7 +791,7 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
             }
             maxrel = sg[0] > 0.0 ? mx / sg[0] : 0.0;
             dtheta = sum;
-            converged = mx <= o->tol * sg[0] || sg[0] == 0.0;
+            converged = mx <= est_tol * sg[0] || sg[0] == 0.0;
             return cudaSuccess;
         };
         if ((e = upload(c, T, sv.B)) != cudaSuccess) return fail("T upload");
@@ -724,7 +802,38 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
             ++svd_fp64;
             if ((e = projected(true)) != cudaSuccess) return fail("projected SVD (FP64)");
         }
-        if (converged || cycle == o->maxit - 1) break;
+        if (converged || cycle == o->maxit - 1) {
+            // the estimate is met (or the cycles ran out): Rayleigh-Ritz output and true residuals
+            if ((e = finalize()) != cudaSuccess) return fail("Rayleigh-Ritz step");
+            if (!true_resid) break;  // k > 32: the estimate decides
+            if (maxrel <= o->tol || sg[0] == 0.0) {
+                converged = 1;
+                break;
+            }
+            converged = 0;
+            if (cycle == o->maxit - 1) break;
+            // refinement: the true residual misses tol.  After 4-digit products the kept
+            // relation A V_kk = U_kk T_kk carries their rounding, which later cycles never
+            // recompute: with k <= b the next cycle starts afresh (full-precision products)
+            // from the top b Ritz vectors, which hold the k wanted ones.  Otherwise the cycles
+            // go on from the same restart state with a tighter estimate target.
+            if (c.tc_digits < 8) {
+                c.tc_digits = 8;
+                fresh = k <= b;
+            } else {
+                est_tol *= 0.5;
+            }
+            ++refines;
+        }
+        if (fresh) {  // explicit restart: V[:, 0:b] = V Q[:, 0:b], orthonormalised
+            e = launch_rotate<float>(c.st, V, ldv, ell, sv.Q, ell, b, V2, ldv, m);
+            if (e == cudaSuccess) e = orthonormalize(c, V2, ldv, b, nullptr, ldv, 0, m, R);
+            if (e != cudaSuccess) return fail("explicit restart");
+            std::swap(V, V2);
+            std::fill(T.begin(), T.end(), 0.0);
+            ++restarts;
+            continue;
+        }
         // thick restart: keep kk Ritz vectors, spike block from S_last
         e = launch_rotate<float>(c.st, U, ldu, ell, sv.P, ell, kk, U2, ldu, n);
         if (e == cudaSuccess) e = launch_rotate<float>(c.st, V, ldv, ell, sv.Q, ell, kk, V2, ldv, m);
@@ -750,71 +859,6 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
             for (int cc = 0; cc < b; ++cc) T[i + (size_t)ell * (kk + cc)] = SP[cc + (size_t)b * i];
         }
         ++restarts;
-    }
-    // output: U P[:, :k], V Q[:, :k]; for k <= 32 refined by one Rayleigh-Ritz
-    // step on span(V Q[:, :k]) with FP32-grade products (W = A V_k, W^T W = Y
-    // Lambda Y^T in FP64, sigma = sqrt(lambda), V = V_k Y, U = W Y / sigma),
-    // whose singular values are accurate to the square of the subspace angle,
-    // and the true residuals ||A^T u_i - sigma_i v_i|| from one more product
-    float* Uo = reinterpret_cast<float*>(W + oOutU);
-    float* Vo = reinterpret_cast<float*>(W + oOutV);
-    c.tc_digits = 8;  // the Rayleigh-Ritz step and the residuals at full precision
-    if (k <= kMaxB) {
-        float* Vk = V2;  // m x k (ldv)
-        float* Wk = U2;  // n x k (ldu)
-        std::vector<double> G, lam, Y, Rk;
-        e = launch_rotate<float>(c.st, V, ldv, ell, sv.Q, ell, k, Vk, ldv, m);
-        if (e == cudaSuccess) e = orthonormalize(c, Vk, ldv, k, nullptr, ldv, 0, m, Rk);
-        if (e == cudaSuccess) e = block_product(c, false, Vk, ldv, Wk, ldu, k);
-        if (e == cudaSuccess) e = gram(c, Wk, ldu, k, Wk, ldu, k, n, c.d_small);
-        if (e == cudaSuccess) e = download(c, c.d_small, G, (size_t)k * k);
-        if (e != cudaSuccess) return fail("Rayleigh-Ritz step");
-        sym_eig(k, G, lam, Y);
-        std::vector<int> ord(k);
-        for (int i = 0; i < k; ++i) ord[i] = i;
-        std::sort(ord.begin(), ord.end(), [&](int a, int b2) { return lam[a] > lam[b2]; });
-        std::vector<double> Cv((size_t)k * k), Cu((size_t)k * k), Cs((size_t)k * k, 0.0);
-        for (int j = 0; j < k; ++j) {
-            const double sj = std::sqrt(std::max(0.0, lam[ord[j]]));
-            sg[j] = sj;
-            for (int r = 0; r < k; ++r) {
-                Cv[r + (size_t)k * j] = Y[r + (size_t)k * ord[j]];
-                Cu[r + (size_t)k * j] = sj > 0.0 ? Y[r + (size_t)k * ord[j]] / sj : 0.0;
-            }
-            Cs[j + (size_t)k * j] = sj;
-        }
-        e = upload(c, Cv, c.d_small);
-        if (e == cudaSuccess) {
-            k_block_axpy<<<axpy_grid(c, m), 256, 0, c.st>>>(Vo, m, k, Vk, ldv, k, c.d_small, k, 0.f, 1.f, m);
-            e = cudaStreamSynchronize(c.st);  // d_small is reused below
-        }
-        if (e == cudaSuccess) e = upload(c, Cu, c.d_small);
-        if (e == cudaSuccess) {
-            k_block_axpy<<<axpy_grid(c, n), 256, 0, c.st>>>(Uo, n, k, Wk, ldu, k, c.d_small, k, 0.f, 1.f, n);
-            e = cudaStreamSynchronize(c.st);
-        }
-        // true residuals: Z = A^T U - V diag(sigma), r_i = ||Z_i||
-        if (e == cudaSuccess) e = block_product(c, true, Uo, n, Vk, ldv, k);
-        if (e == cudaSuccess) e = upload(c, Cs, c.d_small);
-        if (e == cudaSuccess) {
-            k_block_axpy<<<axpy_grid(c, m), 256, 0, c.st>>>(Vk, ldv, k, Vo, m, k, c.d_small, k, 1.f, -1.f, m);
-            e = cudaStreamSynchronize(c.st);
-        }
-        if (e == cudaSuccess) e = gram(c, Vk, ldv, k, Vk, ldv, k, m, c.d_small);
-        if (e == cudaSuccess) e = download(c, c.d_small, G, (size_t)k * k);
-        if (e != cudaSuccess) return fail("Rayleigh-Ritz step");
-        c.launches += 3;
-        double mxr = 0.0, sumr = 0.0;
-        for (int i = 0; i < k; ++i) {
-            res[i] = std::sqrt(std::max(0.0, G[i + (size_t)k * i]));
-            mxr = std::max(mxr, res[i]);
-            sumr += res[i];
-        }
-        maxrel = sg[0] > 0.0 ? mxr / sg[0] : 0.0;
-        dtheta = sumr;
-    } else {
-        e = launch_rotate<float>(c.st, U, ldu, ell, sv.P, ell, k, Uo, n, n);
-        if (e == cudaSuccess) e = launch_rotate<float>(c.st, V, ldv, ell, sv.Q, ell, k, Vo, m, m);
     }
     if (e == cudaSuccess) e = launch_sign_fix<float>(c.st, Uo, n, Vo, m, k, reinterpret_cast<int*>(W + oSigns));
     // U, V out (device-to-device, or to host memory with o->out_host); the
@@ -875,6 +919,7 @@ int run_block(gkl_handle* h, const gkl_opts* o, double* sigma, float* Uout, floa
             info->ms_rmv = sum_event_pairs(c.ev_rmv, c.used_rmv, &info->n_rmv);
         }
         info->jacobi_sweeps = max_sweeps;
+        info->refine_cycles = refines;
     }
     cudaFree(ws);
     cudaEventDestroy(ev0);

@@ -51,7 +51,8 @@ class Info(ctypes.Structure):
                 ("n_rmv", ctypes.c_int64), ("ms_mv", ctypes.c_double), ("ms_rmv", ctypes.c_double),
                 ("jacobi_sweeps", ctypes.c_int32), ("svd_fallbacks", ctypes.c_int32),
                 ("svd_clusters", ctypes.c_int32), ("rank", ctypes.c_int32), ("ms_svd", ctypes.c_double),
-                ("ms_cgs", ctypes.c_double), ("second_u", ctypes.c_int32), ("second_v", ctypes.c_int32)]
+                ("ms_cgs", ctypes.c_double), ("second_u", ctypes.c_int32), ("second_v", ctypes.c_int32),
+                ("refine_cycles", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -54,7 +54,9 @@ def test_block_admixture(gk, b, ell):
     h = gk.GKL(to_dev(g.packed), g.n)
     r = h.svd(k=k, ell=ell, precision="block", block=b, tol=1e-6, maxit=200, seed=9)
     check(M, ref, r, k)
-    assert (r.info["matvec_pairs"] - k) % b == 0  # blocks of b, plus the k of the Rayleigh-Ritz step
+    # blocks of b, plus k per Rayleigh-Ritz step (one, and one more per refinement)
+    assert (r.info["matvec_pairs"] - k * (1 + r.info["refine_cycles"])) % b == 0
+    assert r.info["converged"] and r.info["max_rel_resid"] <= 1e-6
 
 
 def test_block_ragged_sizes(gk):
