@@ -533,16 +533,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_rmv_tc(const __grid_constant__ 
 // The samples are cut into blocks of kMissBlock; segment (b, j) lists the
 // missing samples of SNP j in block b as 16-bit offsets into the block,
 // ascending, padded with kMissPad to a multiple of 8 entries (one 16-byte
-// load).  Segments are stored block-major, off[b m + j] is the first entry of
+// load); kMissPad is the offset of a zero slot just past the block, so the
+// gather needs no test per entry.  Segments are stored block-major, off[b m + j] is the first entry of
 // segment (b, j) and off[nb m] the list's length.  Per product one CTA holds
 // the z values of one block in shared memory and gathers them there for a
 // chunk of SNPs: the list is read once from HBM (2 bytes an entry) and the
 // gathers never leave the SM.
 
-constexpr int kMissBlock = 24576;       // samples a block: its int64 z values fill 192 KB of shared memory
-constexpr uint16_t kMissPad = 0xFFFFu;  // padding entry (above every offset in a block)
+constexpr int kMissBlock = 24576;                // samples a block: its int64 z values fill 192 KB of shared memory
+constexpr uint16_t kMissPad = (uint16_t)kMissBlock;  // padding entry: the zero slot after the block's z values
+constexpr int kMissSlots = kMissBlock + 16;       // z values, zero slot, padding to 16 bytes
 constexpr int kMissThreads = 1024;
-static_assert(kMissBlock % 16 == 0 && kMissBlock < kMissPad, "block of the missing-code list");
+static_assert(kMissBlock % 16 == 0 && kMissBlock < 65536, "block of the missing-code list");
 
 // Missing-code mask of packed word wd of a row (bit 2 s set where sample 16 wd + s has code 3),
 // samples at or above n cleared.
@@ -628,27 +630,33 @@ __device__ __forceinline__ void miss_load(const uint4* __restrict__ src, MissSeg
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         const int64_t e = g.e0 + sl + 8 * r;
-        q[r] = e < g.e1 ? __ldcs(src + e) : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+        constexpr uint32_t kPad2 = (uint32_t)kMissPad * 0x10001u;
+        q[r] = e < g.e1 ? __ldcs(src + e) : make_uint4(kPad2, kPad2, kPad2, kPad2);
     }
 }
 
+// Eight list entries (one 16-byte load): each offset is clamped to the zero
+// slot (a corrupt offset is counted in bad and adds nothing), then its z value
+// is added.
 template <typename ZT>
-__device__ __forceinline__ void miss_gather(const uint4 q, const ZT* zs, int cnt, long long& zh, long long& zl,
-                                            bool& bad) {
-    const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
+__device__ __forceinline__ void miss_gather(uint4 q, const ZT* zs, long long& zh, long long& zl, uint32_t& bad) {
+    constexpr uint32_t kPad2 = (uint32_t)kMissPad * 0x10001u;
+    uint32_t wv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const uint32_t cl = __vminu2(wv[c], kPad2);
+        bad |= wv[c] ^ cl;
+        wv[c] = cl;
+    }
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-        const uint32_t o = (wv[c >> 1] >> (16 * (c & 1))) & 0xFFFFu;
-        if (o < (uint32_t)cnt) {
-            const long long zi = (long long)zs[o];
-            if constexpr (sizeof(ZT) == 4) {
-                zl += zi;
-            } else {
-                zh += zi >> 30;
-                zl += zi & ((1LL << 30) - 1);
-            }
-        } else if (o != kMissPad) {
-            bad = true;
+        const uint32_t o = c & 1 ? wv[c >> 1] >> 16 : wv[c >> 1] & 0xFFFFu;
+        const long long zi = (long long)zs[o];
+        if constexpr (sizeof(ZT) == 4) {
+            zl += zi;
+        } else {
+            zh += zi >> 30;
+            zl += zi & ((1LL << 30) - 1);
         }
     }
 }
@@ -668,13 +676,13 @@ __global__ void __launch_bounds__(kMissThreads, 1) k_miss_sum(const int64_t* __r
     const int64_t s0 = (int64_t)blockIdx.x * per, s1 = min(nseg, s0 + per);
     const double sc = ldexp(dsc[0], -bits);
     const uint4* src = reinterpret_cast<const uint4*>(idx);
-    bool bad = false;
+    uint32_t bad = 0u;
     for (int64_t b = s0 / m; s0 < s1 && b * m < s1; ++b) {
         const int64_t a0 = max(s0, b * m), a1 = min(s1, (b + 1) * m);
         const int64_t z0 = b * kMissBlock;
         const int cnt = (int)min((int64_t)kMissBlock, zlen - z0);
         __syncthreads();  // the previous block's gathers are done
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) zs[i] = z[z0 + i];
+        for (int i = threadIdx.x; i < kMissSlots; i += blockDim.x) zs[i] = i < cnt ? z[z0 + i] : (ZT)0;
         __syncthreads();
         MissSeg cur = miss_seg(off, a0 + grp, a1);
         MissSeg nxt = miss_seg(off, a0 + kGroups + grp, a1);
@@ -686,9 +694,9 @@ __global__ void __launch_bounds__(kMissThreads, 1) k_miss_sum(const int64_t* __r
             const MissSeg nn = miss_seg(off, sb + 2 * kGroups + grp, a1);  // batch t + 2
             long long zh = 0, zl = 0;
 #pragma unroll
-            for (int r = 0; r < 4; ++r) miss_gather<ZT>(q[r], zs, cnt, zh, zl, bad);
+            for (int r = 0; r < 4; ++r) miss_gather<ZT>(q[r], zs, zh, zl, bad);
             for (int64_t e = cur.e0 + 32 + sl; e < cur.e1; e += 8)  // entries beyond the first 256
-                miss_gather<ZT>(__ldcs(src + e), zs, cnt, zh, zl, bad);
+                miss_gather<ZT>(__ldcs(src + e), zs, zh, zl, bad);
 #pragma unroll
             for (int o = 4; o > 0; o >>= 1) {
                 zh += __shfl_xor_sync(0xffffffffu, zh, o);
@@ -701,7 +709,7 @@ __global__ void __launch_bounds__(kMissThreads, 1) k_miss_sum(const int64_t* __r
             for (int r = 0; r < 4; ++r) q[r] = qn[r];
         }
     }
-    if (bad) atomicCAS(err, 0, 51);  // an offset outside its block: skipped, reported
+    if (bad) atomicCAS(err, 0, 51);  // an offset outside its block: clamped to the zero slot, reported
 }
 
 // ---- finishing kernel ----------------------------------------------------------
@@ -843,9 +851,9 @@ bool tc_prepare(gkl_handle* h) {
                              Fx<kDigitsF64>::kSmem) != cudaSuccess)
         return false;
     if (cudaFuncSetAttribute(k_miss_sum<int>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kMissBlock * (int)sizeof(int)) != cudaSuccess ||
+                             kMissSlots * (int)sizeof(int)) != cudaSuccess ||
         cudaFuncSetAttribute(k_miss_sum<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kMissBlock * (int)sizeof(long long)) != cudaSuccess)
+                             kMissSlots * (int)sizeof(long long)) != cudaSuccess)
         return false;
     // list of missing codes per (sample block, SNP), built once: counts, host prefix sum of the
     // padded counts, fill
@@ -912,7 +920,7 @@ cudaError_t launch_rmatvec_tc(const gkl_handle* h, const T* u, T* x, void* scrat
     k_rmv_tc<D><<<p.grid, kThreads, Fx<D>::kSmem, st>>>(map, a);
     if (ev1) cudaEventRecord(ev1, st);
     GKL_DEBUG_SYNC(st, "k_rmv_tc");
-    k_miss_sum<ZT><<<(unsigned)p.miss_grid, kMissThreads, kMissBlock * sizeof(ZT), st>>>(
+    k_miss_sum<ZT><<<(unsigned)p.miss_grid, kMissThreads, kMissSlots * sizeof(ZT), st>>>(
         h->miss_off, h->miss_idx, h->m, p.nb, z, (int64_t)p.nstages * kStageSamples, Fx<D>::kBits, dsc, p3, err);
     GKL_DEBUG_SYNC(st, "k_miss_sum");
     FinArgs f{};
