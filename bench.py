@@ -463,6 +463,43 @@ def run_profile(args):
     return 0
 
 
+PROFILE_SLAB = "slab_200k_x_38912"
+
+
+def run_profile_products(args):
+    """Products only, for ncu captures: args.reps FP32 A.v and A^T u (and with
+    --block-vectors q, the 8-digit tensor-core block products of q vectors) on
+    a workload of synth.CONFIGS, or on the slab of large_200k_x_1m with all
+    200,000 samples and its first 38,912 SNP rows (152 tiles of 256 SNPs: one
+    A^T u work item per SM; 1.95 GB packed)."""
+    from dataclasses import replace
+    import torch
+    import synth
+    from paper_1808_03374_gb300 import build, gkl
+    build()
+    name = args.profile_products
+    geno = (replace(synth.CONFIGS["large_200k_x_1m"].geno, m=38_912) if name == PROFILE_SLAB
+            else synth.CONFIGS[name].geno)
+    packed, _, _ = synth.genotypes_device(geno)
+    h = gkl.GKL(packed, geno.n)
+    v = torch.tensor(synth.normal_vec(31, 0, geno.m), dtype=torch.float32, device="cuda")
+    u = torch.tensor(synth.normal_vec(31, 1, geno.n), dtype=torch.float32, device="cuda")
+    q = args.block_vectors
+    if q:
+        V = torch.tensor(synth.normal_vec(31, 2, q * geno.m).reshape(q, geno.m), dtype=torch.float32, device="cuda")
+        U = torch.tensor(synth.normal_vec(31, 3, q * geno.n).reshape(q, geno.n), dtype=torch.float32, device="cuda")
+    for _ in range(args.reps):
+        h.matvec(v)
+        h.rmatvec(u)
+        if q:
+            h.matmat(V)
+            h.matmat(U, transpose=True)
+    torch.cuda.synchronize()
+    h.sync()
+    print(json.dumps({"profile_products": name, "n": geno.n, "m": geno.m, "reps": args.reps, "block_vectors": q}))
+    return 0
+
+
 def run_paper_model(args):
     """The paper's own workload: its synthetic genotype model (section 2,
     Algorithm 1) at 41,505 markers x 81,700 patients, top 10 singular triplets
@@ -581,6 +618,10 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="only set up and run one benchmark step (for profiler launch lists)")
     ap.add_argument("--profile-workload", default=WORKLOAD, help=argparse.SUPPRESS)
+    ap.add_argument("--profile-products", default=None, metavar="WORKLOAD",
+                    help="only run --reps FP32 A.v + A^T u products on WORKLOAD (for ncu captures)")
+    ap.add_argument("--reps", type=int, default=3, help=argparse.SUPPRESS)
+    ap.add_argument("--block-vectors", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--paper-model", action="store_true",
                     help="the paper's synthetic model at its Table 3 size: solvers side by side (one JSON line)")
     ap.add_argument("--cpu-table", action="store_true",
@@ -597,6 +638,8 @@ def main():
         return run_cpu_pairs(args)
     if args.profile:
         return run_profile(args)
+    if args.profile_products:
+        return run_profile_products(args)
     if args.paper_model:
         return run_paper_model(args)
     if args.impl == "reference":
