@@ -272,6 +272,19 @@ def true_resid(h, res):
     return worst / res.sigma[0]
 
 
+def true_resid64(h, res):
+    """The same residual from the library's FP64 products, one vector at a time
+    (for FP64 solves, whose residuals lie below FP32 rounding)."""
+    import torch
+    worst = 0.0
+    for i in range(res.U.shape[1]):
+        u = res.U[:, i].double().contiguous()
+        v = res.V[:, i].double().contiguous()
+        s = float(res.sigma[i])
+        worst = max(worst, torch.linalg.norm(h.rmatvec(u) - s * v).item(), torch.linalg.norm(h.matvec(v) - s * u).item())
+    return worst / res.sigma[0]
+
+
 def solve_kw(w, **extra):
     return dict(k=w.k, ell=w.ell, reorth=w.reorth, precision=w.precision, tol=w.tol, maxit=3000, seed=7, **extra)
 
@@ -530,6 +543,7 @@ def run_paper_model(args):
                      ("GKL (PRO) FP64, l=128", dict(ell=128, reorth="partial", precision="fp64", tol=1e-8)),
                      ("GKL (FRO, TR) FP32, restart after 20", dict(ell=20, reorth="full", precision="fp32", tol=1e-6)),
                      ("GKL (PRO, TR) FP32, l=50", dict(ell=50, reorth="partial", precision="fp32", tol=1e-6)),
+                     ("GKL (DGKS, TR) FP32, l=50", dict(ell=50, reorth="dgks", precision="fp32", tol=1e-6)),
                      ("block b=16 l=128, tensor-core products", dict(ell=128, precision="block", block=16, k_keep=48,
                                                                      tol=1e-6))):
         run(**kw)  # warm-up
@@ -583,6 +597,58 @@ def run_cpu_pairs(args):
     return 0
 
 
+TABLE_WORKLOADS = ("fp64_full_1k_x_10k", "fp32_pro_10k_x_100k", "grad_20k_x_200k", "block_50k_x_500k")
+
+
+def run_solver_table(args):
+    """Every solver form on the smaller workloads (the 200,000 x 1,000,000
+    one is the benchmark itself): time to the top-k, vector pairs, restarts,
+    and the true residual max_i max(||A^T u_i - s_i v_i||, ||A v_i - s_i u_i||) / s_1
+    from the 8-digit tensor-core block products.  One JSON line."""
+    import torch
+    import synth
+    from paper_1808_03374_gb300 import build, gkl
+    build()
+    solvers = [
+        ("fp64 dgks", dict(precision="fp64", reorth="dgks", tol=1e-10, ell=None)),
+        ("fp32 dgks", dict(precision="fp32", reorth="dgks", tol=1e-6, ell=None)),
+        ("fp32 full", dict(precision="fp32", reorth="full", tol=1e-6, ell=None)),
+        ("fp32 partial", dict(precision="fp32", reorth="partial", tol=1e-6, ell=None)),
+        ("fp32 onesided", dict(precision="fp32", reorth="onesided", tol=1e-6, ell=None)),
+        ("block b16", dict(precision="block", block=16, k_keep=48, tol=1e-6, ell=128)),
+        ("block16 b32", dict(precision="block16", block=32, k_keep=64, tol=1e-6, ell=128)),
+    ]
+    out = {"solver_table": []}
+    for name in TABLE_WORKLOADS:
+        w = synth.CONFIGS[name]
+        packed, _, _ = synth.genotypes_device(w.geno)
+        h = gkl.GKL(packed, w.geno.n)
+        row = {"workload": name, "n": w.geno.n, "m": w.geno.m, "k": w.k, "solvers": {}}
+        for label, kw in solvers:
+            kw = dict(kw)
+            ell = kw.pop("ell") or w.ell
+            if kw["precision"].startswith("block") and w.k >= ell:
+                continue
+            h.svd(k=w.k, ell=ell, maxit=3000, seed=7, raise_on_fail=False, **kw)  # warm-up (allocations)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = h.svd(k=w.k, ell=ell, maxit=3000, seed=7, raise_on_fail=False, **kw)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            row["solvers"][label] = {"ms": dt * 1e3, "pairs": int(r.info["matvec_pairs"]),
+                                     "restarts": int(r.info["restarts"]), "converged": bool(r.converged),
+                                     "tol": kw["tol"],
+                                     "true_max_rel_resid": (true_resid64(h, r) if kw["precision"] == "fp64"
+                                                            else true_resid(h, r)),
+                                     "reported_max_rel_resid": float(r.info["max_rel_resid"]),
+                                     "sigma_1": float(r.sigma[0])}
+        out["solver_table"].append(row)
+        del h, packed
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_cpu_table(args):
     """The FP64 CPU oracle per pair at the workloads whose generation and
     timing fit about half a minute each, on all host cores and on one core,
@@ -624,6 +690,8 @@ def main():
     ap.add_argument("--block-vectors", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--paper-model", action="store_true",
                     help="the paper's synthetic model at its Table 3 size: solvers side by side (one JSON line)")
+    ap.add_argument("--solver-table", action="store_true",
+                    help="every solver form on the smaller workloads: time, pairs, true residual (one JSON line)")
     ap.add_argument("--cpu-table", action="store_true",
                     help="the FP64 CPU oracle per pair at several workloads, all cores and one core (one JSON line)")
     ap.add_argument("--cpu-pairs", default=None, help=argparse.SUPPRESS)
@@ -634,6 +702,8 @@ def main():
     args = ap.parse_args()
     if args.cpu_table:
         return run_cpu_table(args)
+    if args.solver_table:
+        return run_solver_table(args)
     if args.cpu_pairs:
         return run_cpu_pairs(args)
     if args.profile:

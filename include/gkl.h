@@ -95,7 +95,9 @@ typedef struct gkl_opts {
                            the results there and synchronises); zero: device memory */
     int32_t reserved0;  /* must be 0 */
     double tol;         /* converged when max_{i<k} r_i <= tol * sigma_1, r_i the Ritz residual */
-    double omega;       /* PARTIAL / ONESIDED trigger level; 0 = 1e-8 (FP64) or sqrt(eps_fp32) (FP32) */
+    double omega;       /* PARTIAL / ONESIDED trigger level; 0 = min(1e-8 (FP64) or sqrt(eps_fp32) = 2^-12
+                           (FP32), 10 tol), at least 10 unit roundoffs: the output's true residual follows the
+                           orthogonality kept, about 0.1 omega sigma_1 */
     uint64_t seed;      /* counter-based generator seed for the start vector and breakdown restarts */
     const void* v0;     /* optional start vector (device, m entries of the precision's type); NULL = random */
 } gkl_opts;

@@ -380,7 +380,11 @@ static int run_svd(gkl_handle* h, const gkl_opts* o, double* sigma, T* Uout, T* 
     sv.partials = reinterpret_cast<double*>(base + oPart);
     sv.coef = reinterpret_cast<double*>(base + oCoef);
     sv.eps_w = sizeof(T) == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
-    sv.omega = o->omega > 0.0 ? o->omega : (sizeof(T) == 8 ? 1e-8 : 2.44140625e-04);
+    // partial / one-sided trigger level: the true residual of the output follows the
+    // orthogonality kept (measured about 0.1 omega sigma_1), so the default is
+    // min(1e-8 (FP64) or 2^-12 (FP32), 10 tol), and at least 10 eps_w
+    sv.omega = o->omega > 0.0 ? o->omega
+                              : std::min(sizeof(T) == 8 ? 1e-8 : 2.44140625e-04, std::max(10.0 * o->tol, 10.0 * sv.eps_w));
     sv.tol = o->tol;
     sv.seed = o->seed;
 
@@ -476,6 +480,34 @@ static int run_svd(gkl_handle* h, const gkl_opts* o, double* sigma, T* Uout, T* 
     D.launches += 4;
     if ((st = D.check(launch_rotate<T>(h->stream, D.U, ldu, ell, sv.P, ell, k, Uo, n, n), "U out"))) return st;
     if ((st = D.check(launch_rotate<T>(h->stream, D.V, ldv, ell, sv.Q, ell, k, Vo, m, m), "V out"))) return st;
+    // One-sided reorthogonalisation leaves the vectors of the side that was not
+    // reorthogonalised at every step with that basis's loss of orthogonality.
+    // They are recomputed from the other side, v_i = A^T u_i (or u_i = A v_i),
+    // and orthonormalised in order; the values below the numerical rank keep
+    // theirs.
+    const int rank0 = numerical_rank(ho->sg, k, sv.eps_w);
+    if (o->reorth == GKL_REORTH_ONESIDED) {
+        const bool from_u = n <= m;  // the side kept orthonormal at every step
+        const int64_t len = from_u ? m : n;
+        T* W = from_u ? Vo : Uo;
+        for (int i = 0; i < rank0; ++i) {
+            int nl = 0;
+            T* dst = W + (int64_t)i * len;
+            cudaError_t e = from_u ? launch_rmatvec<T>(h, Uo + (int64_t)i * n, dst, h->scratch, nullptr, nullptr,
+                                                       nullptr, nullptr, &nl)
+                                   : launch_matvec<T>(h, Vo + (int64_t)i * m, dst, h->scratch, nullptr, nullptr,
+                                                      nullptr, nullptr, &nl);
+            D.launches += nl;
+            if ((st = D.check(e, "one-sided recomputation"))) return st;
+            if (i == 0) {
+                if ((st = D.cgs(CGS_UPD_NORM, dst, len, W, len, 0, nullptr, ROLE_START, 0))) return st;
+                if ((st = D.scale(dst, len, &sv.sc->scale_v))) return st;
+            } else if ((st = D.orthonormalise(dst, len, W, len, i, ROLE_START, 0, false, &sv.sc->scale_v))) {
+                return st;
+            }
+        }
+        D.products += (rank0 + 1) / 2;  // one product per vector: half a pair
+    }
     if ((st = D.check(launch_sign_fix<T>(h->stream, Uo, n, Vo, m, k, D.signs), "sign"))) return st;
     // U, V out: device-to-device, or device-to-host with o->out_host
     if (Uout && (st = D.check(cudaMemcpyAsync(Uout, Uo, sizeof(T) * n * k, cudaMemcpyDefault, h->stream), "U copy")))

@@ -95,11 +95,13 @@ def test_admixture_small(gk, precision, reorth):
     M, ref, r = run_pair(gk, g, 10, 28, tol, precision, reorth)
     sig_rel = 1e-10 if precision == "fp64" else 1e-5
     vec_eps = 1e-13 if precision == "fp64" else 3e-6
-    omega = 0.0 if reorth in ("full", "dgks") else (1e-8 if precision == "fp64" else 2.0 ** -12)
+    omega = 0.0 if reorth in ("full", "dgks") else min(1e-8 if precision == "fp64" else 2.0 ** -12, 10 * tol)
     check_against_oracle(M, ref, r, 10, sig_rel, vec_eps, omega)
     i = r.info
+    # one-sided runs recompute the other side's k vectors at the end: half a pair each
+    pairs = i["matvec_pairs"] - ((10 + 1) // 2 if reorth == "onesided" else 0)
     if reorth == "partial":
-        assert i["reorth_u"] < i["matvec_pairs"]
+        assert i["reorth_u"] < pairs
     if reorth in ("full", "partial"):
         assert i["second_u"] == 0 and i["second_v"] == 0  # both passes always run, uncounted
     if reorth == "dgks":
@@ -108,8 +110,8 @@ def test_admixture_small(gk, precision, reorth):
         assert i["second_u"] < i["reorth_u"] // 2 and i["second_v"] < i["reorth_v"] // 2
     if reorth == "onesided":
         # n < m: u (the shorter side) every step, v only when its estimate asks
-        assert i["reorth_u"] >= i["matvec_pairs"] - i["cycles"]
-        assert i["reorth_v"] < i["matvec_pairs"]
+        assert i["reorth_u"] >= pairs - i["cycles"]
+        assert i["reorth_v"] < pairs
 
 
 def test_tiny_ragged_and_k1(gk):
@@ -232,6 +234,6 @@ def test_full_size_fp32_partial_residuals():
     for i in range(w.k):
         ra = np.linalg.norm(M.matvec(V[:, i]) - r.sigma[i] * U[:, i]) / s1
         rb = np.linalg.norm(M.rmatvec(U[:, i]) - r.sigma[i] * V[:, i]) / s1
-        assert ra < 2e-5 and rb < 1e-5 + 2 * r.resid[i] / s1
+        assert ra < 2 * w.tol and rb < 2 * w.tol  # omega = 10 tol keeps the true residual within tol
     edge = np.sqrt(1 - w.geno.miss_rate) * (np.sqrt(g.n) + np.sqrt(g.m))
     assert (r.sigma[:4] > 1.1 * edge).all() and r.sigma[4] < 1.05 * edge
