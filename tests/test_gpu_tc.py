@@ -122,3 +122,25 @@ def test_products_after_solves_that_grow_the_outputs(gk):
         xo = M.rmatvec(u.astype(np.float64))
         assert np.all(np.abs(x - xo) <= bound(M, u.astype(np.float64), xo))
     h.sync()
+
+
+# The missing-code list is cut into sample blocks of 24,576 with 16-bit offsets;
+# its gather takes the first 256 entries of a segment in one batch and walks the
+# rest.  Sizes at and around the block edges (a last block of one sample), and
+# missing rates whose segments run past the batch (30%: about 7,400 entries a
+# segment), in both precisions.
+@pytest.mark.parametrize("n,m,miss", [(24_576, 97, 0.05), (24_577, 96, 0.3), (49_153, 40, 0.01),
+                                      (73_729, 33, 0.3), (300, 1_001, 0.9)])
+def test_missing_list_block_edges(gk, n, m, miss):
+    import torch
+    g = small_geno(n, m, miss=miss, seed=n + m)
+    M = oracle_matrix(g)
+    h = handle(gk, g)
+    u64 = synth.normal_vec(19, 2, n)
+    xo = M.rmatvec(u64)
+    x64 = h.rmatvec(torch.tensor(u64, device="cuda")).cpu().numpy()
+    assert np.abs(x64 - xo).max() <= 1e-12 * np.abs(xo).max()
+    u = u64.astype(np.float32)
+    x = h.rmatvec(torch.tensor(u, device="cuda")).double().cpu().numpy()
+    xo32 = M.rmatvec(u.astype(np.float64))
+    assert np.all(np.abs(x - xo32) <= bound(M, u.astype(np.float64), xo32))
