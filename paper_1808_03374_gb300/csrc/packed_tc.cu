@@ -204,7 +204,7 @@ __device__ __forceinline__ uint32_t e2m1_digit(int dg) {
 // at K positions 8 w .. 8 w + 7 (K position kk of sample loc in the chunk:
 // 16 (loc / 16) + even/odd order within the 16, as the decode emits it).
 // Writes their z values and, for every digit row p < D, the word of 8
-// nibbles: image[chunk][p][w].
+// nibbles: image[chunk][p][w ^ 4 (p & 7)] (chunk-swizzled rows, below).
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_u_digits_f4(const T* __restrict__ u, const float* __restrict__ s, int64_t n,
                                                       int64_t nwords, const double* __restrict__ dsc,
@@ -238,9 +238,11 @@ __global__ void __launch_bounds__(256) k_u_digits_f4(const T* __restrict__ u, co
         }
         word[0] |= e2m1_digit((int)r) << (4 * e);  // r in {-1, 0, 1}: |z| <= 8^(D-1)
     }
-    uint32_t* dst = image + chunk * (D * kUnitWords) + w;
+    // row p's 16-byte chunk c is stored at chunk c ^ (p & 7), so that the digit
+    // warp's lanes (one row each) read different shared-memory banks
+    uint32_t* dst = image + chunk * (D * kUnitWords);
 #pragma unroll
-    for (int p = 0; p < D; ++p) dst[p * kUnitWords] = word[p];
+    for (int p = 0; p < D; ++p) dst[p * kUnitWords + (w ^ ((p & 7) << 2))] = word[p];
 }
 
 // ---- main kernel ------------------------------------------------------------
@@ -402,7 +404,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rmv_tc(const __grid_constant__ 
                                                                           (h * D + prow) * kUnitWords * 4);
 #pragma unroll
                         for (int c = 0; c < 8; ++c) {
-                            const uint4 q = src[c];
+                            const uint4 q = src[c ^ (prow & 7)];
                             v[4 * c] = q.x;
                             v[4 * c + 1] = q.y;
                             v[4 * c + 2] = q.z;
