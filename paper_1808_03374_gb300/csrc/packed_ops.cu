@@ -124,7 +124,7 @@ MvPlan plan_products(const gkl_handle* h) {
         const int sms = std::max(1, h->num_sms);
         const int64_t tiles = (p.nwords + 255) / 256;
         double best = 0.0;
-        for (int waves = 1; waves <= 12; ++waves) {
+        for (int waves = 1; waves <= 32; ++waves) {
             int64_t chunks = std::max<int64_t>(1, (waves * (int64_t)sms + tiles - 1) / tiles);
             int64_t rpc = (h->m + chunks - 1) / chunks;
             rpc = std::max<int64_t>(rpc, 256);
