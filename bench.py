@@ -241,13 +241,15 @@ def run_reference(args):
     g, M = oracle_slab(w)
     time_oracle_pairs(M, w.geno.m, 1e9, max(0, args.warmup))
     pairs, dt, rate = time_oracle_pairs(M, w.geno.m, 1e9, args.steps)
-    ms_full = 1e3 / rate
+    # a step is one pair over the slab; its measured time is the step time, and the
+    # value counts the full-matrix pairs that the slab's share of the entries makes up
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "pairs/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_full, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, pairs),
+            "ms_per_full_matrix_pair": 1e3 / rate, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": w.geno.n, "m": w.geno.m,
-                       "step": f"one A.v + A^T.u pair of the FP64 oracle over the first {M.m} SNP rows, "
-                               f"reported per full-matrix pair ({w.geno.m} SNPs)"},
+                       "step": f"one A.v + A^T.u pair of the FP64 oracle over the first {M.m} SNP rows; "
+                               f"value in full-matrix pairs ({w.geno.m} SNPs) per second"},
             "cpu_baseline": {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
                              "sample": f"{pairs} oracle pairs over {M.m} of {w.geno.m} SNP rows ({dt:.1f} s)"},
             "e2e": {"value": rate, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
