@@ -177,10 +177,13 @@ int gkl_set_weights(gkl_handle* h, const float* s, const float* w);
 int gkl_matvec(gkl_handle* h, int prec, const void* v, void* y);
 
 /* x = A^T u.  prec as for gkl_matvec; u (device, n entries), x (device, m).
- * Stream-ordered; does not synchronise.  The FP32 product runs on the tensor
- * cores with bounded pipeline waits; a wait that runs out (never expected) is
- * reported by the next call that synchronises the stream (gkl_sync, gkl_svd,
- * gkl_grad). */
+ * Stream-ordered; does not synchronise.  Both precisions run on the tensor
+ * cores in exact fixed point (u~ = s o u scaled by a power of two S > max|u~|
+ * and rounded to 30 fractional bits for GKL_FP32, 57 for GKL_FP64; the sums are
+ * exact integers, rounded once to the output type), with bounded pipeline
+ * waits; a wait that runs out (never expected) is reported by the next call
+ * that synchronises the stream (gkl_sync, gkl_svd, gkl_grad).
+ * Deterministic. */
 int gkl_rmatvec(gkl_handle* h, int prec, const void* u, void* x);
 
 /* Block products of the block form on the tensor cores (tcgen05):
