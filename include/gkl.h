@@ -155,9 +155,15 @@ int gkl_colstats(const uint8_t* packed, int64_t n, int64_t m, int64_t stride,
  * mu, scale (host or device, m doubles each): copied in.  If both are NULL the
  *   handle computes them with gkl_colstats.
  * stream: cudaStream_t (as void*) used for all later work; NULL = default.
- * Allocates device memory for its own state (released by gkl_destroy).
+ * Allocates device memory for its own state (released by gkl_destroy),
+ *   the largest part a list of the missing codes read by gkl_rmatvec: samples
+ *   in blocks of 24,576, per (block, SNP) the missing samples' 16-bit offsets
+ *   padded to a multiple of 8, about 2 bytes per missing code plus 16 bytes
+ *   per (block, SNP) (4.2 GB for 2*10^9 missing codes at 200,000 x 1,000,000).
+ *   It reads the packed buffer twice to build it and synchronises the stream.
  * Errors: GKL_ERR_ARG (sizes, alignment, exactly one of mu/scale NULL),
- *   GKL_ERR_CUDA. On error *h is NULL. */
+ *   GKL_ERR_CUDA (also when the tensor-core products cannot be set up). On
+ *   error *h is NULL. */
 int gkl_init(gkl_handle** h, const uint8_t* packed, int64_t n, int64_t m, int64_t stride,
              const double* mu, const double* scale, void* stream);
 
