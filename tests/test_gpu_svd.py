@@ -72,6 +72,11 @@ def check_against_oracle(M, ref, r, k, sig_rel, vec_eps, omega=0.0):
     # sign rule: largest-|.| entry of each v is positive
     idx = np.argmax(np.abs(V), axis=0)
     assert np.all(V[idx, np.arange(k)] > 0)
+    # centring (1^T A = 0): 1^T u_i = -1^T r_i / sigma_i for the residual r_i of A v_i = sigma_i u_i
+    n = U.shape[0]
+    csum = np.abs(U.sum(axis=0))
+    cbar = np.sqrt(n) * (2 * np.maximum(r.resid, 0) + (50 * vec_eps + omega) * ref.sigma[0]) / ref.sigma[:k] + 1e-5
+    assert np.all(csum <= cbar), (csum, cbar)
     # reported residuals bound the true ones (a-posteriori, computed by the oracle)
     for i in range(k):
         t = np.linalg.norm(M.rmatvec(U[:, i]) - r.sigma[i] * V[:, i])
