@@ -24,7 +24,7 @@ namespace gkl {
 namespace {
 constexpr int kThreads = 256;   // threads per block of the product kernels
 constexpr int kRowBatch = 32;   // SNP rows staged per batch
-constexpr int kMvBoxBytesHost = 256, kMvRowsHost = 32;  // TMA box of the FP32 A v kernel
+constexpr int kMvBoxBytesHost = 256, kMvRowsHost = 16;  // TMA box of the FP32 A v kernel
 }
 
 // ------------------------------------------------------------------ stats
@@ -117,9 +117,9 @@ MvPlan plan_products(const gkl_handle* h) {
     p.rows_per_chunk = (int)rpc;
     p.chunks = (int)((h->m + rpc - 1) / rpc);
     p.ldp = p.nwords * 16;
-    // FP32 A.v (TMA-fed pair-table kernel, one CTA of 256 words per SM): the SNP
-    // chunking that gives the busiest SM the fewest rows, every chunk at least
-    // one 256-row table batch (rows a multiple of the 32-row stage)
+    // FP32 A.v (TMA-fed pair-table kernel, CTAs of 256 words): the SNP chunking
+    // that gives the busiest SM the fewest rows, every chunk at least one
+    // 256-row table batch (rows a multiple of 32, two 16-row stages)
     {
         const int sms = std::max(1, h->num_sms);
         const int64_t tiles = (p.nwords + 255) / 256;
@@ -259,25 +259,25 @@ __device__ __forceinline__ void pair_lookups(uint32_t wa, uint32_t wb, uint32_t 
 // The FP32 A v kernel: one CTA per (sample tile of 256 words = 4,096 samples,
 // SNP chunk), 8 consumer warps (one 16-sample word per thread) and one copy
 // warp.  The copy warp's lane 0 streams the tile's rows through a ring of
-// shared-memory stages with TMA (32 rows x four 256-byte boxes per stage, no
+// shared-memory stages with TMA (16 rows x four 256-byte boxes per stage, no
 // swizzle: a warp's 32 words of a row are 128 contiguous bytes, one wavefront),
 // so the consumers only wait on full stages and spend their issue slots on
-// table lookups.  Pair tables are built per 256-row batch by consumer threads
+// table lookups; two CTAs share an SM (82 KB of shared memory each).  Pair tables are built per 256-row batch by consumer threads
 // (double-buffered; the consumers meet at a named barrier once per batch).
 constexpr int kMvWords = 256;                  // words (16 samples each) per tile
 constexpr int kMvConsumers = kMvWords;         // consumer threads
 constexpr int kMvThreads = kMvConsumers + 32;  // + one copy warp
-constexpr int kMvRows = 32;                    // rows per stage
+constexpr int kMvRows = 16;                    // rows per stage
 constexpr int kMvBoxBytes = 256;               // box width (bytes of one row)
 constexpr int kMvBoxes = kMvWords * 4 / kMvBoxBytes;
-constexpr int kMvStageBytes = kMvRows * kMvWords * 4;  // 32 KB
+constexpr int kMvStageBytes = kMvRows * kMvWords * 4;  // 16 KB
 constexpr int kMvStages = 4;
 constexpr int kMvTabOff = kMvStages * kMvStageBytes;      // two table buffers of 8 KB
 constexpr int kMvBarOff = kMvTabOff + 2 * kPairTab * 4;
 constexpr int kMvSmem = 1024 + kMvBarOff + 256;
 static_assert(kPairRows % kMvRows == 0, "a table batch covers whole stages");
 
-__global__ void __launch_bounds__(kMvThreads, 1)
+__global__ void __launch_bounds__(kMvThreads, 2)
     k_mv_pair(const __grid_constant__ CUtensorMap tmap, int64_t nwords, int64_t m, int rpc,
               const float* __restrict__ lut, float* __restrict__ part, int64_t ldp, int* err) {
     extern __shared__ uint8_t mv_smem_raw[];
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kMvThreads, 1)
     };
 
     if (warp == kMvConsumers / 32) {
-        // ---- copies: rows j0 .. of this tile, four 256-byte boxes per 32-row stage
+        // ---- copies: rows j0 .. of this tile, four 256-byte boxes per 16-row stage
         if (lane == 0) {
             const int x0 = (int)blockIdx.x * kMvWords * 4;
             int s_it = 0;
