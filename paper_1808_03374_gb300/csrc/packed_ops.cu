@@ -262,8 +262,11 @@ __device__ __forceinline__ void pair_lookups(uint32_t wa, uint32_t wb, uint32_t 
 // shared-memory stages with TMA (16 rows x four 256-byte boxes per stage, no
 // swizzle: a warp's 32 words of a row are 128 contiguous bytes, one wavefront),
 // so the consumers only wait on full stages and spend their issue slots on
-// table lookups; two CTAs share an SM (82 KB of shared memory each).  Pair tables are built per 256-row batch by consumer threads
-// (double-buffered; the consumers meet at a named barrier once per batch).
+// table lookups.  Three CTAs share an SM (three 16 KB stages and 16 KB of
+// tables each, 72 registers a thread): more warps to keep the shared-memory
+// pipe that bounds the kernel busy.  Pair tables are built per 256-row batch by
+// consumer threads (double-buffered; the consumers meet at a named barrier
+// once per batch).
 constexpr int kMvWords = 256;                  // words (16 samples each) per tile
 constexpr int kMvConsumers = kMvWords;         // consumer threads
 constexpr int kMvThreads = kMvConsumers + 32;  // + one copy warp
@@ -271,13 +274,13 @@ constexpr int kMvRows = 16;                    // rows per stage
 constexpr int kMvBoxBytes = 256;               // box width (bytes of one row)
 constexpr int kMvBoxes = kMvWords * 4 / kMvBoxBytes;
 constexpr int kMvStageBytes = kMvRows * kMvWords * 4;  // 16 KB
-constexpr int kMvStages = 4;
+constexpr int kMvStages = 3;
 constexpr int kMvTabOff = kMvStages * kMvStageBytes;      // two table buffers of 8 KB
 constexpr int kMvBarOff = kMvTabOff + 2 * kPairTab * 4;
 constexpr int kMvSmem = 1024 + kMvBarOff + 256;
 static_assert(kPairRows % kMvRows == 0, "a table batch covers whole stages");
 
-__global__ void __launch_bounds__(kMvThreads, 2)
+__global__ void __launch_bounds__(kMvThreads, 3)
     k_mv_pair(const __grid_constant__ CUtensorMap tmap, int64_t nwords, int64_t m, int rpc,
               const float* __restrict__ lut, float* __restrict__ part, int64_t ldp, int* err) {
     extern __shared__ uint8_t mv_smem_raw[];
