@@ -652,14 +652,17 @@ def run_solver_table(args):
 
 
 def run_cpu_table(args):
-    """The FP64 CPU oracle per pair at the workloads whose generation and
-    timing fit about half a minute each, on all host cores and on one core,
-    and one full oracle solve of the small workload; each measurement in its
-    own process."""
+    """The FP64 CPU oracle per pair on all host cores and on one core, full
+    oracle solves (FULL reorthogonalisation, each workload's k, l and tol) of
+    the 1,000 x 10,000, 10,000 x 100,000 and 20,000 x 200,000 workloads on all
+    cores, and pairs of the 50,000 x 500,000 one (the 200,000 x 1,000,000 one
+    is the benchmark line's cpu_baseline); each measurement in its own process.
+    About ten minutes on 16 cores."""
     cores = os.cpu_count() or 1
     plan = [("fp64_full_1k_x_10k", cores, True), ("fp64_full_1k_x_10k", 1, False),
-            ("fp32_pro_10k_x_100k", cores, False), ("fp32_pro_10k_x_100k", 1, False),
-            ("grad_20k_x_200k", cores, False), ("grad_20k_x_200k", 1, False)]
+            ("fp32_pro_10k_x_100k", cores, True), ("fp32_pro_10k_x_100k", 1, False),
+            ("grad_20k_x_200k", cores, True), ("grad_20k_x_200k", 1, False),
+            ("block_50k_x_500k", cores, False)]
     rows = []
     for name, threads, solve in plan:
         cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-pairs", name, "--cpu-threads", str(threads),
