@@ -3,18 +3,19 @@ FP64 CPU oracle and against what the mathematics fixes.
 
 Run on a GPU machine from the repository root:
 
-    python tests/check_large_parity.py null2 cfg3 cfg4 cfg5 --out gpurun_out/large_parity
+    python tests/check_large_parity.py null_10k_x_100k paths_50k_x_500k gradient_20k_x_200k \
+        benchmark_200k_x_1m --out large_parity
 
 Each check prints one JSON line and the run writes a Markdown summary
 (``--out`` + ``.md``) and the JSON lines (``--out`` + ``.jsonl``).  The
 checks, with the pins they rest on:
 
-* ``null2`` -- 10,000 x 100,000, no population structure, 2% missing: the
+* ``null_10k_x_100k`` -- 10,000 x 100,000, no population structure, 2% missing: the
   largest singular value of the standardised matrix sits at the
   Marchenko-Pastur bulk edge sqrt(1 - f) (sqrt(n) + sqrt(m)) (section 2,
   Eqs. 4-5; f the missing fraction, whose entries are 0 after centring), to
   within 2%.
-* ``cfg3`` -- 50,000 x 500,000, 10-population admixture, 1% missing: the
+* ``paths_50k_x_500k`` -- 50,000 x 500,000, 10-population admixture, 1% missing: the
   FP64, FP32 and both block forms solve for k = 20; every triplet's residuals
   ||A v_i - sigma_i u_i|| and ||A^T u_i - sigma_i v_i|| are recomputed with the
   oracle's own products (section 3's convergence criterion, applied a
@@ -22,13 +23,13 @@ checks, with the pins they rest on:
   value within r_i of sigma_i (Weyl), so the FP64 values serve as the
   reference for the other paths' per-value relative errors and subspace
   angles.
-* ``cfg4`` -- 20,000 x 200,000 with per-sample and per-SNP weights
+* ``gradient_20k_x_200k`` -- 20,000 x 200,000 with per-sample and per-SNP weights
   U(0.5, 1.5): the gradient of L = sum_{i<=10} c_i sigma_i^2 + ||S r||^2
   (S the PC scores, r on the well-separated population components) from
   gkl_grad against central differences of FP64 solves at 64 seeded
   coordinates of w and of s, with h = 1e-6 and h = 1e-4, and the sigma part
   against its closed form sigma_i v_ij^2 / w_j.
-* ``cfg5`` -- 200,000 x 1,000,000, 20-population admixture, 1% missing: the
+* ``benchmark_200k_x_1m`` -- 200,000 x 1,000,000, 20-population admixture, 1% missing: the
   FP32 solve and the 8-digit block form, residuals from the oracle's
   products (the oracle reads the 50 GB packed matrix in host memory).
 """
@@ -95,7 +96,7 @@ def host(t):
 
 # ---------------------------------------------------------------- null model
 
-def check_null2(gk):
+def check_null_10k_x_100k(gk):
     w = synth.CONFIGS["fp32_pro_10k_x_100k"]
     spec = synth.null_variant(w.geno)
     P, _, _ = synth.genotypes_device(spec)
@@ -103,14 +104,14 @@ def check_null2(gk):
     r, dt = solve(h, k=5, ell=30, reorth="dgks", precision="fp32", tol=1e-6, maxit=500, seed=3)
     edge = np.sqrt(1.0 - spec.miss_rate) * (np.sqrt(spec.n) + np.sqrt(spec.m))
     rel = float(r.sigma[0] / edge - 1.0)
-    return {"check": "null2", "n": spec.n, "m": spec.m, "converged": bool(r.converged),
+    return {"check": "null_10k_x_100k", "n": spec.n, "m": spec.m, "converged": bool(r.converged),
             "sigma": [float(x) for x in r.sigma], "mp_edge": float(edge), "sigma1_rel_to_edge": rel,
             "solve_s": dt, "pass": bool(r.converged and abs(rel) <= 0.02)}
 
 
-# ---------------------------------------------------------------- config 3
+# ---------------------------------------------------------------- 50,000 x 500,000
 
-def check_cfg3(gk):
+def check_paths_50k_x_500k(gk):
     w = synth.CONFIGS["block_50k_x_500k"]
     spec = w.geno
     P, packed = device_matrix(spec)
@@ -130,7 +131,7 @@ def check_cfg3(gk):
     M = oracle.Matrix.from_packed(packed, spec.n)
     ref = res["fp64"][0]
     Vr = host(ref.V)
-    out = {"check": "cfg3", "n": spec.n, "m": spec.m, "k": k, "paths": {}}
+    out = {"check": "paths_50k_x_500k", "n": spec.n, "m": spec.m, "k": k, "paths": {}}
     ok = True
     for name, (r, dt) in res.items():
         t0 = time.perf_counter()
@@ -160,7 +161,7 @@ def check_cfg3(gk):
     return out
 
 
-# ---------------------------------------------------------------- config 4
+# ---------------------------------------------------------------- 20,000 x 200,000, gradient
 
 def loss_and_grad(gk, h, s, w, c, r, v0=None, tol=1e-13, want_grad=True, seed=5):
     """L = sum c_i sigma_i^2 + ||S r||^2 from an FP64 solve with weights s, w
@@ -182,7 +183,7 @@ def loss_and_grad(gk, h, s, w, c, r, v0=None, tol=1e-13, want_grad=True, seed=5)
     return L, res, host(gs), host(gw)
 
 
-def check_cfg4(gk, ncoords=64):
+def check_gradient_20k_x_200k(gk, ncoords=64):
     import torch
     wl = synth.CONFIGS["grad_20k_x_200k"]
     spec = wl.geno
@@ -249,16 +250,16 @@ def check_cfg4(gk, ncoords=64):
     worst6 = max(abs(x["fd_h1e-6"] - x["grad"]) / (1e-4 * abs(x["grad"]) + x["floor"]) for x in rows)
     worst4 = max(x["rel_err_h1e-4"] for x in rows)
     ok = all(x["pass_h1e-6"] for x in rows) and closed_err <= 1e-8
-    return {"check": "cfg4", "n": spec.n, "m": spec.m, "k": k, "L": L0, "loss_noise": dL,
+    return {"check": "gradient_20k_x_200k", "n": spec.n, "m": spec.m, "k": k, "L": L0, "loss_noise": dL,
             "base_solve_s": t_base, "fd_solves": 4 * len(rows), "fd_pairs": pairs, "fd_s": t_fd,
             "closed_form_sigma_part_max_rel_err": closed_err, "grad_max_abs_w": gmax_w, "grad_max_abs_s": gmax_s,
             "coords_per_side": ncoords, "worst_err_over_bar_h1e-6": float(worst6),
             "worst_rel_err_h1e-4": float(worst4), "rows": rows, "pass": bool(ok)}
 
 
-# ---------------------------------------------------------------- config 5
+# ---------------------------------------------------------------- 200,000 x 1,000,000
 
-def check_cfg5(gk):
+def check_benchmark_200k_x_1m(gk):
     w = synth.CONFIGS["large_200k_x_1m"]
     spec = w.geno
     P, packed = device_matrix(spec)
@@ -279,7 +280,7 @@ def check_cfg5(gk):
     t0 = time.perf_counter()
     rr = oracle_residuals(M, sig, U, V)
     tor = time.perf_counter() - t0
-    out = {"check": "cfg5", "n": spec.n, "m": spec.m, "k": w.k, "oracle_products_s": tor, "paths": {}}
+    out = {"check": "benchmark_200k_x_1m", "n": spec.n, "m": spec.m, "k": w.k, "oracle_products_s": tor, "paths": {}}
     ok = True
     for q, name in enumerate(runs):
         r, dt = res[name]
@@ -296,7 +297,7 @@ def check_cfg5(gk):
     return out
 
 
-CHECKS = {"null2": check_null2, "cfg3": check_cfg3, "cfg4": check_cfg4, "cfg5": check_cfg5}
+CHECKS = {"null_10k_x_100k": check_null_10k_x_100k, "paths_50k_x_500k": check_paths_50k_x_500k, "gradient_20k_x_200k": check_gradient_20k_x_200k, "benchmark_200k_x_1m": check_benchmark_200k_x_1m}
 
 
 def markdown(results):
@@ -306,10 +307,10 @@ def markdown(results):
     for r in results:
         lines.append(f"## {r['check']}: n = {r['n']:,}, m = {r['m']:,} -- {'PASS' if r['pass'] else 'FAIL'}")
         lines.append("")
-        if r["check"] == "null2":
+        if r["check"] == "null_10k_x_100k":
             lines.append(f"sigma_1 = {r['sigma'][0]:.4f}, Marchenko-Pastur edge sqrt(1-f)(sqrt n + sqrt m) = "
                          f"{r['mp_edge']:.4f}, relative {r['sigma1_rel_to_edge']:+.4%} (bar 2%).")
-        elif r["check"] in ("cfg3", "cfg5"):
+        elif r["check"] in ("paths_50k_x_500k", "benchmark_200k_x_1m"):
             lines.append("| path | converged | solve s | pairs | oracle max r_i/sigma_1 | library's | "
                          "max sigma rel err vs FP64 | max angle vs FP64 |")
             lines.append("|---|---|---|---|---|---|---|---|")
@@ -322,7 +323,7 @@ def markdown(results):
                 lines.append("")
                 lines.append(f"max |sigma_fp32 - sigma_block| / sigma_fp32 = "
                              f"{r['sigma_max_rel_diff_fp32_vs_block']:.2e}")
-        elif r["check"] == "cfg4":
+        elif r["check"] == "gradient_20k_x_200k":
             lines.append(f"{r['coords_per_side']} coordinates of w and of s; {r['fd_solves']} FP64 solves "
                          f"({r['fd_pairs']} pairs, {r['fd_s']:.1f} s).  Loss L = {r['L']:.6e}, evaluation noise "
                          f"{r['loss_noise']:.2e}.")
@@ -339,15 +340,15 @@ def markdown(results):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("checks", nargs="+", choices=sorted(CHECKS))
-    ap.add_argument("--out", default=os.path.join("gpurun_out", "large_parity"))
-    ap.add_argument("--coords", type=int, default=64, help="cfg4: coordinates per weight vector")
+    ap.add_argument("--out", default="large_parity", help="path prefix of the .md and .jsonl records")
+    ap.add_argument("--coords", type=int, default=64, help="gradient_20k_x_200k: coordinates per weight vector")
     args = ap.parse_args()
     oracle.build()
     gk = _lib()
     results = []
     os.makedirs(os.path.dirname(args.out) or ".", exist_ok=True)
     for name in args.checks:
-        r = CHECKS[name](gk, args.coords) if name == "cfg4" else CHECKS[name](gk)
+        r = CHECKS[name](gk, args.coords) if name == "gradient_20k_x_200k" else CHECKS[name](gk)
         results.append(r)
         print(json.dumps({k: v for k, v in r.items() if k != "rows"}), flush=True)
         with open(args.out + ".jsonl", "a") as f:
