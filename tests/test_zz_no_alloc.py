@@ -5,13 +5,15 @@ loops where an allocation's device-wide synchronisation is not allowed) get a
 product whose scratch is a fixed array inside the library.  This file is
 collected last so that a run stopping at its first failure has already run
 every other test.  It checks, through the C ABI, that two calls in a row agree
-with gkl_matvec on the same inputs, and that oversized problems are refused.
+with gkl_matvec and with the oracle's product on the same inputs, and that
+oversized problems are refused.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -29,8 +31,14 @@ def setup():
     return gkl, g, packed, mu, scale, h
 
 
+@pytest.fixture(scope="module")
+def oracle_mat(setup):
+    g = setup[1]
+    return oracle.Matrix.from_packed(g.packed, g.n)
+
+
 @pytest.mark.parametrize("prec,tol", [(0, 1e-13), (1, 2e-5)])
-def test_noalloc_matches_matvec_twice(setup, prec, tol):
+def test_noalloc_matches_matvec_and_oracle_twice(setup, oracle_mat, prec, tol):
     import torch
     gkl, g, packed, mu, scale, h = setup
     dt = torch.float64 if prec == 0 else torch.float32
@@ -48,6 +56,8 @@ def test_noalloc_matches_matvec_twice(setup, prec, tol):
         a, b = y.double().cpu().numpy(), ref.double().cpu().numpy()
         assert np.isfinite(a).all()
         assert np.linalg.norm(a - b) <= tol * np.linalg.norm(b)
+        yo = oracle_mat.matvec(v.double().cpu().numpy())
+        assert np.linalg.norm(a - yo) <= tol * np.linalg.norm(yo)
 
 
 def test_noalloc_rejects_sizes_beyond_static_scratch(setup):
