@@ -119,6 +119,30 @@ def test_admixture_small(gk, precision, reorth):
         assert i["reorth_v"] < pairs
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_onesided_tall(gk, precision):
+    """One-sided reorthogonalisation with more samples than SNPs: the v side
+    (the shorter) is reorthogonalised at every step, the u side by its
+    estimate, and the k output u vectors are recomputed as A v_i."""
+    g = small_geno(6007, 1503, pops=5, miss=0.02, seed=43)
+    tol = 1e-10 if precision == "fp64" else 1e-6
+    M, ref, r = run_pair(gk, g, 10, 28, tol, precision, "onesided")
+    vec_eps = 1e-13 if precision == "fp64" else 3e-6
+    omega = min(1e-8 if precision == "fp64" else 2.0 ** -12, 10 * tol)
+    check_against_oracle(M, ref, r, 10, 1e-10 if precision == "fp64" else 1e-5, vec_eps, omega)
+    i = r.info
+    pairs = i["matvec_pairs"] - (10 + 1) // 2
+    assert i["reorth_v"] >= pairs - i["cycles"]
+    assert i["reorth_u"] < pairs
+    # the recomputed u vectors are orthonormal and satisfy A v_i = sigma_i u_i to the residual
+    U = r.U.double().cpu().numpy()
+    V = r.V.double().cpu().numpy()
+    assert np.abs(U.T @ U - np.eye(10)).max() < (1e-12 if precision == "fp64" else 1e-5)
+    for j in range(10):
+        t = np.linalg.norm(M.matvec(V[:, j]) - r.sigma[j] * U[:, j])
+        assert t <= 2 * max(r.resid[j], 0) + (50 * vec_eps + omega) * ref.sigma[0]
+
+
 def test_tiny_ragged_and_k1(gk):
     g = small_geno(37, 301, pops=2, miss=0.1, seed=5)
     M, ref, r = run_pair(gk, g, 1, 4, 1e-12, "fp64", "full")
