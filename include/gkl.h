@@ -178,11 +178,13 @@ int gkl_set_weights(gkl_handle* h, const float* s, const float* w);
 
 /* y = A v.  prec = GKL_FP64 (v, y double) or GKL_FP32 (float).
  * v (device, m entries), y (device, n entries); y must not alias v.
+ * GKL_ERR_ARG if either is not device memory of the handle's GPU.
  * Stream-ordered; does not synchronise.  Deterministic: partial sums over SNP
  * chunks are combined in a fixed order. */
 int gkl_matvec(gkl_handle* h, int prec, const void* v, void* y);
 
-/* x = A^T u.  prec as for gkl_matvec; u (device, n entries), x (device, m).
+/* x = A^T u.  prec as for gkl_matvec; u (device, n entries), x (device, m);
+ * GKL_ERR_ARG if either is not device memory of the handle's GPU.
  * Stream-ordered; does not synchronise.  Both precisions run on the tensor
  * cores in exact fixed point (u~ = s o u scaled by a power of two S > max|u~|
  * and rounded to 30 fractional bits for GKL_FP32, 57 for GKL_FP64; the sums are
@@ -204,8 +206,8 @@ int gkl_rmatvec(gkl_handle* h, int prec, const void* u, void* x);
  *   of its largest entry) plus the final rounding to FP32.
  * Allocates its scratch per call (digit tiles, partial sums) and synchronises
  * the stream.  GKL_ERR_ARG if the tensor-core path is unavailable for this
- * handle (packed buffer not 16-byte aligned, or n > 524,000) or arguments are
- * out of range; GKL_ERR_CUDA on a CUDA error or a pipeline wait that ran out. */
+ * handle (packed buffer not 16-byte aligned, or n > 524,000), X or Y is not
+ * device memory of the handle's GPU, or arguments are out of range; GKL_ERR_CUDA on a CUDA error or a pipeline wait that ran out. */
 int gkl_matmat(gkl_handle* h, int32_t transpose, int32_t q, int32_t digits, const float* X, int64_t ldx, float* Y,
                int64_t ldy);
 
@@ -284,6 +286,8 @@ int gkl_scores(gkl_handle* h, void* S, int32_t out_host);
  *   complement of V_k.
  * g_w (device, m entries) and g_s (device, n entries), either may be NULL:
  *   dL/dw and dL/ds in the last solve's type.  Weights must be nonzero.
+ *   GKL_ERR_ARG if sigma_bar is not host memory, or scores_bar, g_w or g_s
+ *   not device memory of the handle's GPU.
  * Synchronises the stream.  Errors: GKL_ERR_STATE (no converged solve, or the
  * weights changed since), GKL_ERR_GAP, GKL_NOT_CONVERGED (a solve did not
  * converge), GKL_ERR_ARG, GKL_ERR_CUDA (including a tensor-core product whose

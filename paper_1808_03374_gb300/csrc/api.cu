@@ -695,6 +695,8 @@ int gkl_set_weights(gkl_handle* h, const float* s, const float* w) {
 int gkl_matvec(gkl_handle* h, int prec, const void* v, void* y) {
     if (!h) return set_err(nullptr, GKL_ERR_ARG, "NULL handle");
     if (!v || !y || v == y) return set_err(h, GKL_ERR_ARG, "v and y must be distinct non-NULL device buffers");
+    if (mem_kind(v, h->device) != MEM_DEVICE || mem_kind(y, h->device) != MEM_DEVICE)
+        return set_err(h, GKL_ERR_ARG, "v and y must be device memory of the handle's GPU");
     if (prec != GKL_FP64 && prec != GKL_FP32) return set_err(h, GKL_ERR_ARG, "unknown precision %d", prec);
     MvPlan p = plan_products(h);
     int st = ensure_scratch(h, p.bytes_fp64);
@@ -708,6 +710,8 @@ int gkl_matvec(gkl_handle* h, int prec, const void* v, void* y) {
 int gkl_rmatvec(gkl_handle* h, int prec, const void* u, void* x) {
     if (!h) return set_err(nullptr, GKL_ERR_ARG, "NULL handle");
     if (!u || !x || u == x) return set_err(h, GKL_ERR_ARG, "u and x must be distinct non-NULL device buffers");
+    if (mem_kind(u, h->device) != MEM_DEVICE || mem_kind(x, h->device) != MEM_DEVICE)
+        return set_err(h, GKL_ERR_ARG, "u and x must be device memory of the handle's GPU");
     if (prec != GKL_FP64 && prec != GKL_FP32) return set_err(h, GKL_ERR_ARG, "unknown precision %d", prec);
     MvPlan p = plan_products(h);
     int st = ensure_scratch(h, p.bytes_fp64);

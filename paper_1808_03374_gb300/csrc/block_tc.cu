@@ -792,6 +792,8 @@ extern "C" int gkl_matmat(gkl_handle* h, int32_t transpose, int32_t q, int32_t d
     const int64_t rin = transpose ? h->n : h->m, rout = transpose ? h->m : h->n;
     if (!X || !Y || q < 1 || q > 32 || (digits != 4 && digits != 8) || ldx < rin || ldy < rout)
         return set_err(h, GKL_ERR_ARG, "gkl_matmat: need X, Y non-NULL, 1 <= q <= 32, digits 4 or 8, ld >= rows");
+    if (mem_kind(X, h->device) != MEM_DEVICE || mem_kind(Y, h->device) != MEM_DEVICE)
+        return set_err(h, GKL_ERR_ARG, "gkl_matmat: X and Y must be device memory of the handle's GPU");
     if (!block_tc_prepare(h))
         return set_err(h, GKL_ERR_ARG, "gkl_matmat: tensor-core block products unavailable for this handle");
     void* scratch = nullptr;
@@ -803,14 +805,6 @@ extern "C" int gkl_matmat(gkl_handle* h, int32_t transpose, int32_t q, int32_t d
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (scratch) cudaFree(scratch);
     if (e != cudaSuccess) return cuda_err(h, e, "gkl_matmat");
-    int terr = 0;
-    int* ew = reinterpret_cast<int*>(reinterpret_cast<char*>(h->aux) + kAuxErrOffset);
-    if ((e = cudaMemcpy(&terr, ew, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
-        return cuda_err(h, e, "gkl_matmat error word");
-    if (terr) {
-        cudaMemset(ew, 0, sizeof(int));
-        return set_err(h, GKL_ERR_CUDA, "tensor-core block product: a pipeline wait ran out (code %d)", terr);
-    }
-    return GKL_OK;
+    return take_pending_error(h);  // a tensor-core pipeline wait that ran out (read and cleared on h's stream)
 }
 

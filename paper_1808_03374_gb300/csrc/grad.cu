@@ -292,6 +292,11 @@ extern "C" int gkl_grad(gkl_handle* h, const double* sigma_bar, const void* scor
                        "gkl_grad needs a converged gkl_svd on this handle, with the current weights, first");
     if (!g_w && !g_s) return set_err(h, GKL_ERR_ARG, "nothing to compute: g_w and g_s are both NULL");
     if (!(min_relgap >= 0.0)) return set_err(h, GKL_ERR_ARG, "min_relgap must be >= 0");
+    for (const void* p : {scores_bar, static_cast<const void*>(g_w), static_cast<const void*>(g_s)})
+        if (p && mem_kind(p, h->device) != MEM_DEVICE)
+            return set_err(h, GKL_ERR_ARG, "scores_bar, g_w and g_s must be device memory of the handle's GPU");
+    if (sigma_bar && mem_kind(sigma_bar, h->device) != MEM_HOST)
+        return set_err(h, GKL_ERR_ARG, "sigma_bar must be host memory");
     if (h->last_prec == GKL_FP64)
         return run_grad<double>(h, sigma_bar, static_cast<const double*>(scores_bar), static_cast<double*>(g_w),
                                 static_cast<double*>(g_s), min_relgap);

@@ -230,6 +230,25 @@ def test_not_converged_and_argument_errors(gk):
     assert e.value.code == gk.ERR_ARG
     with pytest.raises(gk.GKLError):
         h.svd(k=5, ell=301)  # ell > n
+    # the C entry points reject vectors that are not device memory of the handle's GPU, before any launch
+    import ctypes
+    import torch
+    lib, vp = gk.lib(), ctypes.c_void_p
+    host_m, host_n = np.zeros(2000), np.zeros(300)
+    dev_m = torch.zeros(2000, dtype=torch.float64, device="cuda")
+    dev_n = torch.zeros(300, dtype=torch.float64, device="cuda")
+    hp = lambda a: a.ctypes.data_as(vp)  # noqa: E731
+    dp = lambda t: vp(t.data_ptr())  # noqa: E731
+    assert lib.gkl_matvec(h._h, gk.FP64, hp(host_m), dp(dev_n)) == gk.ERR_ARG
+    assert lib.gkl_matvec(h._h, gk.FP64, dp(dev_m), hp(host_n)) == gk.ERR_ARG
+    assert lib.gkl_rmatvec(h._h, gk.FP64, hp(host_n), dp(dev_m)) == gk.ERR_ARG
+    assert lib.gkl_rmatvec(h._h, gk.FP64, dp(dev_n), hp(host_m)) == gk.ERR_ARG
+    assert b"device memory" in lib.gkl_last_error(h._h)
+    X = np.zeros((2, 2000), dtype=np.float32)
+    Y = torch.zeros((2, 300), dtype=torch.float32, device="cuda")
+    assert lib.gkl_matmat(h._h, 0, 2, 8, hp(X), 2000, dp(Y), 300) == gk.ERR_ARG
+    h.sync()
+    torch.testing.assert_close(h.matvec(dev_m), dev_n)  # the handle is still usable: A 0 = 0
 
 
 def test_solver_deterministic(gk):
