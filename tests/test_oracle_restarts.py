@@ -32,3 +32,14 @@ def test_restart_variants_against_lapack(problem, variant):
     if variant == "ritz":
         ref = oracle.gkl(M, k=k, ell=30, tol=1e-10, v0=v0, maxit=2000)
         assert (r.pairs, r.restarts) == (ref.pairs, ref.restarts)
+
+
+@pytest.mark.parametrize("variant", ["ritz", "harmonic"])
+def test_matrix_free_equals_dense(problem, variant):
+    """The packed operator (the C oracle's products) and its dense copy give
+    the same run: pairs, restarts and values to rounding."""
+    M, A, v0 = problem
+    a = gkl_restarted(A, k=10, ell=30, tol=1e-10, v0=v0, variant=variant)
+    b = gkl_restarted(M, k=10, ell=30, tol=1e-10, v0=v0, variant=variant)
+    assert (a.pairs, a.restarts) == (b.pairs, b.restarts)
+    assert np.max(np.abs(a.sigma - b.sigma) / a.sigma) < 1e-13
