@@ -117,6 +117,20 @@ def _check(code: int, h=None):
         raise GKLError(code, lib().gkl_last_error(h).decode())
 
 
+def _need_buffer(t, shape, dtype=None, cuda=None, what="buffer"):
+    """Raise ValueError unless tensor t has exactly this shape (and dtype,
+    device kind), contiguous: the library takes its sizes from the handle, so a
+    smaller buffer would be read or written past its end."""
+    if tuple(t.shape) != tuple(shape) and not (len(shape) == 1 and t.numel() == shape[0] and t.dim() <= 1):
+        raise ValueError(f"{what}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{what}: expected dtype {dtype}, got {t.dtype}")
+    if cuda is not None and t.is_cuda != cuda:
+        raise ValueError(f"{what}: expected {'device' if cuda else 'host'} memory")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: must be contiguous")
+
+
 def colstats(packed: torch.Tensor, n: int):
     """Per-SNP mean, 1/SD and observed count of a packed matrix (device tensors)."""
     assert packed.is_cuda and packed.dtype == torch.uint8 and packed.dim() == 2 and packed.is_contiguous()
@@ -184,6 +198,10 @@ class GKL:
         self._sync_stream()
         s = None if s is None else s.to(self.device, torch.float32).contiguous()
         w = None if w is None else w.to(self.device, torch.float32).contiguous()
+        if s is not None:
+            _need_buffer(s, (self.n,), what="sample weights s")
+        if w is not None:
+            _need_buffer(w, (self.m,), what="SNP weights w")
         self.generation += 1
         _check(lib().gkl_set_weights(self._h, _ptr(s), _ptr(w)), self._h)
         self._weights = (s, w)
@@ -192,6 +210,7 @@ class GKL:
         prec = FP64 if v.dtype == torch.float64 else FP32
         assert v.is_cuda and v.dtype in (torch.float32, torch.float64) and v.numel() == self.m and v.is_contiguous()
         y = out if out is not None else torch.empty(self.n, dtype=v.dtype, device=self.device)
+        _need_buffer(y, (self.n,), v.dtype, True, "out")
         self._sync_stream()
         _check(lib().gkl_matvec(self._h, prec, _ptr(v), _ptr(y)), self._h)
         return y
@@ -200,6 +219,7 @@ class GKL:
         prec = FP64 if u.dtype == torch.float64 else FP32
         assert u.is_cuda and u.dtype in (torch.float32, torch.float64) and u.numel() == self.n and u.is_contiguous()
         x = out if out is not None else torch.empty(self.m, dtype=u.dtype, device=self.device)
+        _need_buffer(x, (self.m,), u.dtype, True, "out")
         self._sync_stream()
         _check(lib().gkl_rmatvec(self._h, prec, _ptr(u), _ptr(x)), self._h)
         return x
@@ -214,6 +234,7 @@ class GKL:
         assert X.is_contiguous()
         q = X.shape[0]
         Y = out if out is not None else torch.empty((q, rows_out), dtype=torch.float32, device=self.device)
+        _need_buffer(Y, (q, rows_out), torch.float32, True, "out")
         self._sync_stream()
         _check(lib().gkl_matmat(self._h, int(transpose), q, digits, _ptr(X), rows_in, _ptr(Y), rows_out), self._h)
         return Y
@@ -225,7 +246,9 @@ class GKL:
             block: int = 0, out_host: bool = False) -> SVDResult:
         """Top-k triplets.  U and V come back as n x k and m x k views of
         column-major buffers, on the device, or in pinned host memory with
-        out_host=True (the library copies them there)."""
+        out_host=True (the library copies them there).  Caller buffers U and
+        V, if given, are contiguous k x n and k x m tensors of the solve's
+        dtype (the column-major layout); v0 has m entries."""
         prec = _PREC[precision]
         dt = _DTYPE[prec]
         o = Opts()
@@ -235,12 +258,17 @@ class GKL:
         o.block, o.out_host = block, int(out_host)
         if v0 is not None:
             v0 = v0.to(self.device, dt).contiguous()
+            _need_buffer(v0, (self.m,), what="v0")
             o.v0 = v0.data_ptr()
         where = dict(device="cpu", pin_memory=True) if out_host else dict(device=self.device)
         if U is None and want_u:
             U = torch.empty((k, self.n), dtype=dt, **where)  # column-major n x k
         if V is None and want_v:
             V = torch.empty((k, self.m), dtype=dt, **where)
+        if U is not None:
+            _need_buffer(U, (k, self.n), dt, what="U")
+        if V is not None:
+            _need_buffer(V, (k, self.m), dt, what="V")
         sigma = np.zeros(k)
         resid = np.zeros(k)
         info = Info()
@@ -288,8 +316,13 @@ class GKL:
         sb = None
         if sigma_bar is not None:
             sb = np.ascontiguousarray(np.asarray(sigma_bar, dtype=np.float64))
+            if self._last_k() and sb.shape != (self._last_k(),):  # before any solve the library says ERR_STATE
+                raise ValueError(f"sigma_bar: expected {self._last_k()} entries, got shape {sb.shape}")
         Sb = None
         if scores_bar is not None:
+            if self._last_k() and tuple(scores_bar.shape) != (self.n, self._last_k()):
+                raise ValueError(f"scores_bar: expected shape {(self.n, self._last_k())}, "
+                                 f"got {tuple(scores_bar.shape)}")
             Sb = scores_bar.to(self.device, dtype).t().contiguous()  # column-major n x k
         gw = torch.empty(self.m, dtype=dtype, device=self.device) if want_w else None
         gs = torch.empty(self.n, dtype=dtype, device=self.device) if want_s else None

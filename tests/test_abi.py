@@ -98,3 +98,21 @@ def test_struct_layouts_match_header():
         assert int(got[cname]) == ctypes.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert int(got[f"{cname}.{f}"]) == getattr(cls, f).offset, (cname, f)
+
+
+def test_binding_checks_buffer_sizes_before_the_call():
+    """The library takes every length from the handle, so the binding refuses a
+    caller tensor of the wrong shape, dtype or memory kind before passing its
+    pointer (else the library would read or write past its end)."""
+    import torch
+    from paper_1808_03374_gb300.gkl import _need_buffer
+    _need_buffer(torch.zeros(7), (7,), torch.float32, False, "v")        # accepted
+    _need_buffer(torch.zeros(3, 5, dtype=torch.float64), (3, 5), torch.float64)
+    for t, args in [(torch.zeros(6), ((7,),)),                           # too short
+                    (torch.zeros(8), ((7,),)),                           # too long
+                    (torch.zeros(5, 3), ((3, 5),)),                      # transposed
+                    (torch.zeros(7), ((7,), torch.float64)),             # wrong dtype
+                    (torch.zeros(7), ((7,), None, True)),                # host where device is needed
+                    (torch.zeros(5, 3).t(), ((3, 5),))]:                 # not contiguous
+        with pytest.raises(ValueError):
+            _need_buffer(t, *args)
