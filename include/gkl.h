@@ -223,9 +223,11 @@ int gkl_matmat(gkl_handle* h, int32_t transpose, int32_t q, int32_t digits, cons
  * Scratch: a fixed 32 MiB device array inside the library, held by every GPU
  * that loads the library until the process exits.  A call needs
  * (chunks * 16*ceil(n/16) + 4*m) elements of the precision's type, chunks being
- * the SNP chunk count of the product (4 to 8 blocks per SM over the sample
- * tiles of 128 to 256 words: 196 in FP64 and 228 in FP32 for n = 10,000 on
- * 152 SMs);
+ * the SNP chunk count of the product over sample tiles of 256 words (FP64:
+ * about 4 blocks per SM; FP32: the chunking, over 1 to 32 waves, that gives the
+ * busiest SM the fewest rows).  On 152 SMs, n = 10,000, m = 100,000 takes 196
+ * chunks in FP64 (18.9 MB) and 101 in FP32 (5.6 MB); 200,000 x 1,000,000 needs
+ * more than the array holds in either precision;
  * sizes beyond 32 MiB less 256 bytes (the last 256 hold the error word of the
  * FP32 product's bounded TMA waits, which this call cannot report: it does
  * not synchronise) are rejected with GKL_ERR_ARG and a message that gives both
