@@ -80,7 +80,7 @@ cudaError_t launch_colstats(const uint8_t* packed, int64_t n, int64_t m, int64_t
 // ------------------------------------------------------------------ TMA view for A v
 
 // TMA descriptor of the packed matrix for the FP32 A v kernel: a 2-D uint8
-// tensor (stride x m) read in boxes of 256 bytes x 32 rows, no swizzle.
+// tensor (stride x m) read in boxes of 256 bytes x 16 rows, no swizzle.
 // Host-only (no device memory is allocated); false if the driver entry point
 // is unavailable or the descriptor is rejected.
 bool make_mv_map(const uint8_t* packed, int64_t stride, int64_t m, void* out) {
