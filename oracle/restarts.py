@@ -24,7 +24,8 @@ beyond the expansion's own.
   Ritz values solve (A^T A V y)^T (A^T A V y - theta^2 V y) = 0; with
   A^T A V_l = V B^^T B this gives B^ B^^T (B y) = theta^2 (B y), so they are the
   singular values of B^ = P^ S^ Q^^T, with harmonic Ritz vectors
-  V_l B^-1 p^_i.  Kept (the augmented restart): U p^_i and V q^_i, which
+  V_l B^-1 p^_i.  Kept (the augmented restart, as in Baglama and Reichel's
+  restarted bidiagonalisation methods): U p^_i and V q^_i, which
   satisfy A^T U p^_i = s^_i V q^_i exactly, and the next left vector u_l:
   A V q^_i = s^_i U p^_i + alpha_l Q^[last, i] u_l, so the residual is
   alpha_l |Q^[last, i]|; the expansion then continues from A^T u_l.  After
